@@ -1,0 +1,256 @@
+"""Invariants, brute force and search-level properties of the CPU oracle."""
+import itertools
+import math
+
+import numpy as np
+import pytest
+
+from paper_1909_10286_gb300 import instances as I
+
+
+def _relabelled(inst, pf, pb, ph, ps):
+    """Instance with fields, BPs, HUs and SUs renumbered: new id k = old id p[k]."""
+    B, F = inst.n_bps, inst.n_fields
+    xy = np.concatenate([inst.xy[:1], inst.xy[1:1 + B][pb], inst.xy[1 + B:][pf]])
+    return I.custom_instance(xy, inst.area_ha[pf], inst.supply_t[pf], inst.demand_t[pb], inst.hu_rate_ha_h[ph],
+                             inst.hu_speed_kmh, inst.su_cap_t[ps], inst.su_fill_ha[ps], inst.su_speed_kmh[ps],
+                             inst.n_tours)
+
+
+def test_relabelling_invariance(oracle_mod):
+    """Path length and times do not depend on how fields, BPs and units are numbered."""
+    inst = I.make_instance("paper", 3)
+    o = oracle_mod.Oracle(inst)
+    rng = np.random.default_rng(5)
+    base = o.init_plan()
+    p = oracle_mod.make_params(seed=11)
+    plans = [base] + [o.apply(base, o.move(p, 0, i, base)) for i in range(40)]
+    pf, pb = rng.permutation(inst.n_fields), rng.permutation(inst.n_bps)
+    ph, ps = rng.permutation(inst.n_hu), rng.permutation(inst.n_su)
+    inv_f, inv_b = np.argsort(pf), np.argsort(pb)
+    o2 = oracle_mod.Oracle(_relabelled(inst, pf, pb, ph, ps))
+    for plan in plans:
+        tours, bps = plan.to_lists()
+        tours2 = [[int(inv_b[b]) for b in t] for t in tours]
+        bps2 = [None] * inst.n_bps
+        for b, fl in enumerate(bps):
+            bps2[int(inv_b[b])] = [int(inv_f[f]) for f in fl]
+        s1 = o.score(plan)
+        s2 = o2.score(oracle_mod.Plan.from_lists(tours2, bps2))
+        assert s1["feasible"] == s2["feasible"]
+        if s1["feasible"]:
+            assert s2["cost"] == pytest.approx(s1["cost"], rel=1e-12)
+            assert s2["tmax"] == pytest.approx(s1["tmax"], rel=1e-12)
+
+
+@pytest.mark.parametrize("wl,seed", [("tiny", 0), ("paper", 1), ("batched", 7)])
+@pytest.mark.parametrize("p_swap,fix", [(0.0, 0), (0.3, 0), (0.0, 1)])
+def test_moves_keep_plans_valid(oracle_mod, wl, seed, p_swap, fix):
+    """Every field and every BP appears exactly once after any move (Sec. 2.4); with a fixed
+    field-to-BP assignment (Sec. 2.6) no field changes its BP."""
+    inst = I.make_instance(wl, seed)
+    o = oracle_mod.Oracle(inst)
+    base = o.init_plan()
+    assert o.validate(base) == 0
+    p = oracle_mod.make_params(seed=seed + 1000, p_swap=p_swap, fix_field_bp=fix)
+    _, bps0 = base.to_lists()
+    owner0 = {f: b for b, fl in enumerate(bps0) for f in fl}
+    for i in range(300):
+        mv = o.move(p, 3, i, base)
+        cand = o.apply(base, mv)
+        assert o.validate(cand) == 0
+        if fix:
+            _, bps = cand.to_lists()
+            assert {f: b for b, fl in enumerate(bps) for f in fl} == owner0
+
+
+def test_identity_move_keeps_cost(oracle_mod):
+    """Reinserting a vertex at its own slot returns the base plan and its cost."""
+    inst = I.make_instance("paper", 2)
+    o = oracle_mod.Oracle(inst)
+    base = o.init_plan()
+    tours, bps = base.to_lists()
+    c0 = o.score(base)["cost"]
+    for b, fl in enumerate(bps):
+        for k, f in enumerate(fl):
+            cand = o.apply(base, np.array([0, f, b, k], np.int16))
+            assert cand == base
+    for g, tl in enumerate(tours):
+        for k, b in enumerate(tl):
+            cand = o.apply(base, np.array([1, b, g, k], np.int16))
+            assert cand == base
+            assert o.score(cand)["cost"] == c0
+
+
+def test_finite_cost_implies_demand_met(oracle_mod):
+    """Eq. 2, checked with independent sums: every plan with a finite cost meets every demand,
+    and every plan that meets them gets a finite ungated cost."""
+    inst = I.make_instance("paper", 4)
+    o = oracle_mod.Oracle(inst)
+    base = o.init_plan()
+    p = oracle_mod.make_params(seed=77, gate=0)
+    sup = inst.supply_t.astype(np.float64)
+    n_inf = 0
+    for i in range(400):
+        cand = o.apply(base, o.move(p, 0, i, base))
+        _, bps = cand.to_lists()
+        met = all(sup[fl].sum() >= inst.demand_t[b] for b, fl in enumerate(bps))
+        s = o.score(cand)
+        assert met == s["feasible"] == math.isfinite(s["cost"])
+        n_inf += not met
+    assert 0 < n_inf < 400
+
+
+def _neighbourhood(tours, bps, n_tours):
+    """All plans one remove-and-reinsert move away (Step 8), built with plain list operations."""
+    out = set()
+    for b, fl in enumerate(bps):
+        for k, f in enumerate(fl):
+            rem = [list(x) for x in bps]
+            del rem[b][k]
+            for bd in range(len(bps)):
+                for pd in range(len(rem[bd]) + 1):
+                    nb = [list(x) for x in rem]
+                    nb[bd].insert(pd, f)
+                    out.add((tuple(map(tuple, tours)), tuple(map(tuple, nb))))
+    for g, tl in enumerate(tours):
+        for k, b in enumerate(tl):
+            rem = [list(x) for x in tours]
+            del rem[g][k]
+            for gd in range(n_tours):
+                for pd in range(len(rem[gd]) + 1):
+                    nt = [list(x) for x in rem]
+                    nt[gd].insert(pd, b)
+                    out.add((tuple(map(tuple, nt)), tuple(map(tuple, bps))))
+    return out
+
+
+def test_sampled_moves_cover_the_neighbourhood(oracle_mod):
+    """With 2^14 candidates on the tiny instance the sampled moves reach exactly the plans one
+    reinsert move away, and the best sampled cost equals the best cost in that neighbourhood."""
+    inst = I.make_instance("tiny", 0)
+    o = oracle_mod.Oracle(inst)
+    base = o.init_plan()
+    tours, bps = base.to_lists()
+    nbh = _neighbourhood(tours, bps, inst.n_tours)
+    p = oracle_mod.make_params(seed=1000, gate=0)
+    seen = set()
+    for i in range(1 << 14):
+        cand = o.apply(base, o.move(p, 0, i, base))
+        t, b = cand.to_lists()
+        seen.add((tuple(map(tuple, t)), tuple(map(tuple, b))))
+    assert seen == nbh
+    best_nbh = min(o.score(oracle_mod.Plan.from_lists([list(x) for x in t], [list(x) for x in b]))["cost"]
+                   for t, b in nbh)
+    r = o.score_batch(p, 0, base, 1 << 14)
+    assert r["cost"].min() == best_nbh
+
+
+def _all_plans(F, B, T):
+    """Every plan of the tiny instance: BPs arranged over tours, fields arranged over BPs."""
+    bp_arr = []
+    for assign in itertools.product(range(T), repeat=B):
+        for perm in itertools.permutations(range(B)):
+            tours = [[b for b in perm if assign[b] == g] for g in range(T)]
+            bp_arr.append(tuple(map(tuple, tours)))
+    bp_arr = sorted(set(bp_arr))
+    fld_arr = []
+    for assign in itertools.product(range(B), repeat=F):
+        for perm in itertools.permutations(range(F)):
+            fld_arr.append(tuple(tuple(f for f in perm if assign[f] == b) for b in range(B)))
+    fld_arr = sorted(set(fld_arr))
+    return bp_arr, fld_arr
+
+
+def test_brute_force_tiny(oracle_mod):
+    """Exhaustive enumeration of the tiny instance (6 fields, 2 BPs, 2 tours): 6 BP
+    arrangements x 5040 field arrangements = 30,240 plans. The search's best cost is a real
+    plan's cost, never below the exhaustive optimum, and without the gate it reaches it."""
+    inst = I.make_instance("tiny", 0)
+    o = oracle_mod.Oracle(inst)
+    bp_arr, fld_arr = _all_plans(inst.n_fields, inst.n_bps, inst.n_tours)
+    assert len(bp_arr) == 6 and len(fld_arr) == 5040
+    best = math.inf
+    n_feas = 0
+    for t in bp_arr:
+        for b in fld_arr:
+            s = o.score(oracle_mod.Plan.from_lists([list(x) for x in t], [list(x) for x in b]))
+            if s["feasible"]:
+                n_feas += 1
+                best = min(best, s["cost"])
+    assert 0 < n_feas < 30240
+    for gate in (0, 1):
+        p = oracle_mod.make_params(eps=0.5, seed=1000, gate=gate)
+        st = o.start(p)
+        r = o.search(p, st, 50, 1 << 12)
+        assert st.cstar >= best - 1e-9
+        assert o.score(st.xbest)["cost"] == pytest.approx(st.cstar, rel=1e-12)
+        if gate == 0:
+            assert st.cstar == pytest.approx(best, rel=1e-12)
+
+
+def test_local_min_against_exhaustive_splits(oracle_mod):
+    """Reported, not asserted as optimal: the HU/SU local minimisation of the tiny instance's
+    initial plan against all 2^3 HU x 2^4 SU splits. It must never beat the true min-max."""
+    inst = I.make_instance("tiny", 0)
+    o = oracle_mod.Oracle(inst)
+    s = o.score(o.init_plan())
+    D = lambda i, j: float(np.hypot(*(inst.xy[i].astype(np.float64) - inst.xy[j].astype(np.float64))))  # noqa
+    tours, bps = o.init_plan().to_lists()
+    B = inst.n_bps
+    L, A = [], []
+    for t in tours:
+        seq = [1 + B + f for b in t for f in bps[b]]
+        L.append(D(0, seq[0]) + sum(D(a, c) for a, c in zip(seq, seq[1:])) + D(seq[-1], 0))
+        A.append(sum(float(inst.area_ha[f]) for b in t for f in bps[b]))
+    best = math.inf
+    for split in itertools.product(range(2), repeat=inst.n_hu):
+        R = [sum(float(inst.hu_rate_ha_h[h]) for h in range(inst.n_hu) if split[h] == g) for g in range(2)]
+        if min(R) == 0:
+            continue
+        best = min(best, max(L[g] / inst.hu_speed_kmh + A[g] / R[g] for g in range(2)))
+    assert s["tmax"] >= best - 1e-12
+    assert s["tmax"] <= 1.5 * best
+
+
+def test_search_monotone_and_resumable(oracle_mod):
+    """C* never rises; with the gate on Tmax* never rises either (Sec. 2.5); a search split
+    into two calls equals one uninterrupted search (counter-based randomness)."""
+    inst = I.make_instance("paper", 0)
+    o = oracle_mod.Oracle(inst)
+    p = oracle_mod.make_params(eps=0.5, seed=1000, gate=1)
+    st = o.start(p)
+    r = o.search(p, st, 12, 2048, threads=4)
+    assert np.all(np.diff(r["cstar"]) <= 0)
+    assert np.all(np.diff(r["tmaxstar"]) <= 0)
+    st_a = o.start(p)
+    ra = o.search(p, st_a, 5, 2048, threads=4)
+    rb = o.search(p, st_a, 7, 2048, threads=4)
+    assert np.array_equal(np.concatenate([ra["istar"], rb["istar"]]), r["istar"])
+    assert st_a.cstar == st.cstar and st_a.xbest == st.xbest and st_a.xold == st.xold
+
+
+def test_eps_rule_extremes(oracle_mod):
+    """Eq. 5: eps = 0 always continues from x_old, eps = 1 always from x*; eps = 0.5 is a coin."""
+    inst = I.make_instance("tiny", 0)
+    o = oracle_mod.Oracle(inst)
+    for eps, lo, hi in ((0.0, 0, 0), (1.0, 1000, 1000), (0.5, 430, 570)):
+        p = oracle_mod.make_params(eps=eps, seed=1000)
+        n = sum(o.eps_select(p, it) for it in range(1000))
+        assert lo <= n <= hi
+
+
+def test_move_distribution(oracle_mod):
+    """Step 8 reading: the vertex is uniform over the F+B vertices (fields drawn F/(F+B) of the
+    time), the destination BP uniform over B."""
+    inst = I.make_instance("paper", 0)
+    o = oracle_mod.Oracle(inst)
+    base = o.init_plan()
+    p = oracle_mod.make_params(seed=5)
+    r = o.score_batch(p, 0, base, 1 << 15, threads=4)
+    mv = r["moves"]
+    F, B = inst.n_fields, inst.n_bps
+    frac_field = np.mean(mv[:, 0] == 0)
+    assert frac_field == pytest.approx(F / (F + B), abs=0.01)
+    dst = np.bincount(mv[mv[:, 0] == 0, 2], minlength=B) / np.sum(mv[:, 0] == 0)
+    assert np.allclose(dst, 1.0 / B, atol=0.01)
