@@ -1,0 +1,305 @@
+"""Benchmark of the candidate search: candidates scored per second.
+
+One step = one iteration of Algorithm 1 (Steps 6-16) on the paper-scale plain
+workload: 40 fields, 5 BPs, 3 tours, 10 HUs, 20 SUs in a 50 x 50 km square,
+2^20 candidates per iteration, every candidate scored exactly (demand check,
+Fig. 1 costs, HU/SU local minimisation, gate), then argmin and update.
+
+Timing: W untimed warm-up iterations, then K iterations each bracketed by CUDA
+events on the search stream; the L2 is flushed (a 256 MiB device write)
+before every timed iteration, outside the events. Under torchrun every rank
+searches its own instance (seed + rank): replicas, weak scaling, no
+collective in the data path; the time is the max over ranks.
+
+Extra keys: e2e (the same metric through the C ABI with the state copied
+from and to pinned host buffers every iteration), roofline (the scoring
+kernel against the issue rate of the SMs, with the work per candidate counted
+by the instrumented CPU oracle on a sample of the same iteration), clocks,
+gpu_launches and cpu_baseline (the oracle on the host cores).
+
+--impl reference times the CPU oracle alone on this workload (a bounded
+sample of candidates per iteration, all host cores).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "candidates scored/s; time to reach within 1% of best cost (learned+batched vs plain)"
+UNIT = "candidates/s"
+WORKLOAD = "paper-scale plain search: 40 fields, 5 BPs, 3 tours, 10 HUs, 20 SUs, 50x50 km, 2^20 candidates/iter"
+L2_FLUSH_BYTES = 256 << 20
+
+
+def _dist():
+    import torch.distributed as dist
+
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    if ws > 1 and not dist.is_initialized():
+        import torch
+        backend = "nccl" if torch.cuda.is_available() else "gloo"
+        dist.init_process_group(backend=backend)
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def _barrier(ws):
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def _max_over_ranks(x: float, ws: int) -> float:
+    if ws == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    dev = "cuda" if torch.cuda.is_available() and dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+class ClockSampler:
+    """nvidia-smi clock samples during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.dev = device_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            import tempfile
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.dev), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, power, reasons = [], [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1])); smax.append(float(parts[2])); power.append(float(parts[3]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        os.remove(self.path)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm), "power_w_max": max(power)}
+
+
+def _peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        return {}
+
+
+def oracle_throughput(inst, params_kw, n_cand, budget_s, threads, max_iters=50, state=None):
+    """The CPU oracle's Algorithm 1 on the host cores: iterations of m candidates
+    (m <= n_cand, chosen so the run takes about budget_s). Returns (cand/s, m, iters, threads)."""
+    from oracle import oracle as O
+
+    o = O.Oracle(inst)
+    op = O.make_params(**params_kw)
+    st = state or o.start(op)
+    probe = min(n_cand, 8192)
+    t0 = time.perf_counter()
+    o.search(op, st.copy(), 1, probe, threads=threads)
+    rate = probe / max(time.perf_counter() - t0, 1e-6)
+    m = int(min(n_cand, max(1024, rate * budget_s / 3)))
+    iters = int(max(1, min(max_iters, budget_s * rate / m)))
+    t0 = time.perf_counter()
+    o.search(op, st, iters, m, threads=threads)
+    dt = time.perf_counter() - t0
+    return m * iters / dt, m, iters, threads
+
+
+def run_reference(args, ws, rank):
+    if rank != 0:
+        return
+    from paper_1909_10286_gb300 import instances as I
+    from oracle import oracle as O
+
+    inst = I.make_instance(args.workload, args.seed)
+    n = args.n_cand or I.SEARCH[args.workload][0]
+    threads = os.cpu_count() or 1
+    kw = dict(eps=0.5, seed=1000 + args.seed, gate=1)
+    o = O.Oracle(inst)
+    op = O.make_params(**kw)
+    st = o.start(op)
+    # sample size: the whole run (warm-up + steps) within about two minutes
+    probe = min(n, 8192)
+    t0 = time.perf_counter()
+    o.search(op, st.copy(), 1, probe, threads=threads)
+    rate = probe / max(time.perf_counter() - t0, 1e-6)
+    m = int(min(n, max(1024, rate * 120.0 / max(1, args.steps + args.warmup))))
+    o.search(op, st, args.warmup, m, threads=threads)
+    t0 = time.perf_counter()
+    o.search(op, st, args.steps, m, threads=threads)
+    dt = time.perf_counter() - t0
+    value = m * args.steps / dt
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3 / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "instance_seed": args.seed, "n_cand_per_iter": n},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
+                             "sample": f"{m} of the {n} candidates per iteration, {args.steps} timed iterations"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="paper")
+    ap.add_argument("--seed", type=int, default=0)
+    ap.add_argument("--n-cand", type=int, default=0)
+    ap.add_argument("--e2e-steps", type=int, default=20)
+    ap.add_argument("--cpu-budget", type=float, default=12.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+    ws, rank, local = _dist()
+    if args.impl == "reference":
+        run_reference(args, ws, rank)
+        return
+
+    import numpy as np
+    import torch
+
+    from paper_1909_10286_gb300 import biolog
+    from paper_1909_10286_gb300 import instances as I
+
+    torch.cuda.set_device(local)
+    n = args.n_cand or I.SEARCH[args.workload][0]
+    inst = I.make_instance(args.workload, args.seed + rank)
+    kw = dict(eps=0.5, seed=1000 + args.seed + rank, gate=1)
+    stream = torch.cuda.Stream()
+    S = biolog.Search([inst], biolog.make_params(n_cand=n, **kw), stream=stream)
+    cfg = S.config()
+    with torch.cuda.stream(stream):
+        S.search_step(args.warmup)
+    torch.cuda.synchronize()
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    clocks = ClockSampler(local)
+    clocks.start()
+    _barrier(ws)
+    torch.cuda.synchronize()
+    with torch.cuda.stream(stream):
+        for a, b in evs:
+            flush.zero_()
+            a.record(stream)
+            S.search_step(1)
+            b.record(stream)
+    torch.cuda.synchronize()
+    _barrier(ws)
+    clk = clocks.stop()
+    t_ms = sum(a.elapsed_time(b) for a, b in evs)
+    t_ms = _max_over_ranks(t_ms, ws)
+    value = n * args.steps * ws / (t_ms / 1e3)
+    ms_step = t_ms / args.steps
+
+    # e2e through the C ABI: state in from pinned host memory, one iteration, state out
+    st = S.get_state()
+    pin = {k: [torch.from_numpy(np.ascontiguousarray(a)).pin_memory() for a in st[k]] for k in ("xold", "xbest")}
+    hstate = dict(xold=[t.numpy() for t in pin["xold"]], xbest=[t.numpy() for t in pin["xbest"]],
+                  cstar=st["cstar"], tmaxstar=st["tmaxstar"], iter=st["iter"])
+    bytes_state = sum(a.nbytes for a in hstate["xold"] + hstate["xbest"]) + 12
+    _barrier(ws)
+    t0 = time.perf_counter()
+    for _ in range(args.e2e_steps):
+        S.set_state(hstate)
+        with torch.cuda.stream(stream):
+            S.search_step(1)
+        out = S.get_state()
+        for k in ("xold", "xbest"):
+            for dst, src in zip(hstate[k], out[k]):
+                dst[...] = src
+        hstate.update(cstar=out["cstar"], tmaxstar=out["tmaxstar"], iter=out["iter"])
+    e2e_s = _max_over_ranks(time.perf_counter() - t0, ws)
+    e2e = {"value": n * args.e2e_steps * ws / e2e_s, "unit": UNIT, "h2d_bytes_per_step": bytes_state,
+           "d2h_bytes_per_step": bytes_state,
+           "api": "bl_set_state + bl_search_step(1) + bl_get_state, pinned host buffers"}
+
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD if args.workload == "paper" else args.workload,
+                       "instance_seed": args.seed, "n_cand_per_iter": n, "eps": 0.5, "gate": 1,
+                       "l2": "flushed before every timed step (256 MiB device write)",
+                       "kernel": cfg, "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU"},
+            "gpu_launches": args.steps * cfg["launches_per_iter"], "clocks": clk, "e2e": e2e}
+
+    if rank == 0:
+        # roofline: oracle-counted model operations per candidate on a sample of this iteration
+        from oracle import oracle as O
+
+        o = O.Oracle(inst)
+        op = O.make_params(**kw)
+        cur = S.get_state()
+        base = O.Plan(*(cur["xbest"] if o.eps_select(op, cur["iter"]) else cur["xold"]))
+        tstar = o.score(O.Plan(*cur["xbest"]), op, gate=0)["tmax"]
+        m = 1 << 14
+        r = o.score_batch(op, cur["iter"], base, m, tmax_star=tstar, threads=os.cpu_count() or 1)
+        w_per = r["ops"] / m
+        peaks = _peaks()
+        f_mhz = float(peaks.get("sm_max_mhz", 2070.0))
+        sms = torch.cuda.get_device_properties(local).multi_processor_count
+        peak = sms * 4 * 32 * f_mhz * 1e6 / 1e12            # lane-ops/s: 4 schedulers x 32 lanes per SM
+        achieved = w_per * n / (ms_step / 1e3) / 1e12
+        line["roofline"] = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tlane-op/s",
+                            "frac": achieved / peak, "traffic": None, "ops_per_candidate": w_per,
+                            "peak_basis": f"{sms} SMs x 4 schedulers x 32 lanes x {f_mhz:.0f} MHz (sm_max_mhz of "
+                                          "MEASURED_PEAKS.json)"}
+        if ws == 1 and not args.no_cpu_baseline:
+            rate, m_s, iters, thr = oracle_throughput(inst, kw, n, args.cpu_budget, os.cpu_count() or 1)
+            line["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": thr, "kind": "oracle",
+                                    "sample": f"{iters} oracle iterations of {m_s} candidates (of {n}) from the "
+                                              "initial plan"}
+        print(json.dumps(line), flush=True)
+    S.close()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

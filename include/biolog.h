@@ -1,0 +1,214 @@
+/*
+ * biolog.h -- C ABI of the GB300 candidate-search library for the biomass
+ * logistics problem of M. G. Plessen, "GPU-accelerated Logistics Optimisation
+ * for Biomass Production with Multiple Simultaneous Harvesters Tours, Fields
+ * and Plants" (arXiv 1909.10286).
+ *
+ * The library runs Algorithm 1 (Sec. 2.5) on one GPU: every iteration draws n
+ * candidate plans with counter-based Philox moves (Step 8), scores each one
+ * exactly -- Eq. 2 demand check, Fig. 1 path-length cost (Sec. 2.2), HU and SU
+ * assignment by local minimisation (Sec. 2.5, Eq. 6, Algorithm 2), and the
+ * completion-time gate -- then takes the argmin and updates the best plan
+ * (Steps 13-16). The whole iteration stays on the device.
+ *
+ * Conventions for every entry point:
+ *   - plain C types only; no exceptions cross the ABI;
+ *   - the return value is BL_OK (0) or a negative BL_E* code, and the message
+ *     of the last failure is available from bl_last_error(handle) (or
+ *     bl_global_error() when no handle exists yet);
+ *   - "host" pointers are CPU memory, "device" pointers are CUDA global memory
+ *     of the current device;
+ *   - calls on one handle are not thread-safe; different handles are
+ *     independent.
+ *
+ * Node numbering: node 0 is the HQ, nodes 1..B the BPs, nodes B+1..B+F the
+ * fields. BP ids and field ids below are 0-based (BP b is node 1+b).
+ *
+ * Plan encoding (Sec. 2.4, decision variables (i)-(iv)), all int16:
+ *   bp_order[B]    BP ids, tours concatenated in tour order, each tour's BPs
+ *                  in visiting order;
+ *   tour_cnt[T]    BPs per tour (0 = inactive tour);
+ *   field_order[F] field ids grouped by BP id (BP 0's fields first), each
+ *                  group in harvest order;
+ *   bp_cnt[B]      fields per BP, indexed by BP id.
+ * Decision variables (v)-(vi), the HUs and SUs per tour, are derived by the
+ * scorer's local minimisation and reported by bl_best_plan.
+ */
+#ifndef BIOLOG_H
+#define BIOLOG_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define BL_OK 0
+#define BL_EINVAL (-1)               /* bad argument, size or value */
+#define BL_EINFEASIBLE_INSTANCE (-2) /* total supply below total demand (Eq. 2 cannot hold) */
+#define BL_ETOO_LARGE (-3)           /* beyond the int16 encoding or the kernel limits below */
+#define BL_ECUDA (-4)                /* a CUDA runtime call failed */
+#define BL_ETIMEOUT (-5)             /* a bounded device-side wait gave up */
+#define BL_ESTATE (-6)               /* call out of order (e.g. a freed or failed handle) */
+
+/* Limits of this build: tours <= 16, HUs <= 64, SUs <= 128, fields <= 32767,
+   BPs <= 1024. The FP32 supplies, HU rates, SU capacities and SU fill areas
+   of one instance must each span at most 2^(52 - 24 - log2(n+1)) in ratio so
+   that their sums are exact in 64-bit fixed point and in FP64. */
+#define BL_MAX_TOURS 16
+#define BL_MAX_HU 64
+#define BL_MAX_SU 128
+#define BL_MAX_FIELDS 32767
+#define BL_MAX_BPS 1024
+
+/* One problem instance (Sec. 2.1, Table 1). Caller-owned, host memory,
+   read only during bl_plan_init*, which copies what it needs. */
+typedef struct bl_instance {
+    int32_t n_fields, n_bps, n_tours, n_hu, n_su;
+    const float *xy;           /* host, (1+B+F) x 2, km */
+    const float *dist;         /* host, optional (1+B+F)^2 row-major km; NULL = straight
+                                  lines from xy (Sec. 3.1), computed in FP64, stored FP32 */
+    const float *area_ha;      /* host, F: field sizes h_f */
+    const float *supply_t;     /* host, F: expected supplies (Eq. 3), > 0 */
+    const float *demand_t;     /* host, B: minimum demands d_b (Eq. 2), > 0 */
+    const float *hu_rate_ha_h; /* host, H: in-field working rate of each HU, > 0 */
+    float hu_speed_kmh;        /* road speed of HUs */
+    const float *su_cap_t;     /* host, S: loading capacity of each SU */
+    const float *su_fill_ha;   /* host, S: hectares harvested while the SU fills */
+    const float *su_speed_kmh; /* host, S: road speed of each SU */
+} bl_instance;
+
+/* Search parameters. */
+typedef struct bl_params {
+    float eps;               /* exploration rule, Eq. 5, in [0, 1] */
+    float p_swap;            /* probability that a move is a swap of two same-type
+                                vertices instead of a reinsert (0 = the paper's Step 8) */
+    uint64_t seed;           /* Philox key */
+    uint32_t inst_idx;       /* Philox counter word 2 of instance 0 (instance k uses inst_idx+k) */
+    int32_t n_cand;          /* candidates per iteration per instance, >= 1 */
+    int32_t fix_field_bp;    /* 1 = a removed field returns to its own BP (Sec. 2.6) */
+    int32_t fix_resources;   /* 1 = keep the initial HU/SU dealing, no local minimisation (Case 2) */
+    int32_t gate;            /* completion-time gate: 0 off, 1 discard Tmax > Tmax*,
+                                2 discard Tmax >= Tmax* (literal reading) */
+    int32_t block_threads;   /* 0 = autotuned; else threads per block of the scorer */
+    int32_t blocks_per_sm;   /* 0 = autotuned; else resident blocks per SM to size the grid */
+    int32_t tile;            /* 0 = autotuned; else candidates per work item */
+    int32_t log_capacity;    /* iterations kept in the per-instance log (0 = 4096) */
+    void *workspace;         /* device, optional: caller-owned buffer of
+                                bl_workspace_bytes() bytes, 256-byte aligned; NULL = the
+                                library allocates and frees its own */
+    size_t workspace_bytes;
+} bl_params;
+
+/* Report of one plan, filled by bl_best_plan. Caller-owned host buffers sized
+   from the instance; any array pointer may be NULL. */
+typedef struct bl_plan {
+    int16_t *bp_order;     /* B */
+    int16_t *tour_cnt;     /* T */
+    int16_t *field_order;  /* F */
+    int16_t *bp_cnt;       /* B */
+    int16_t *hu_tour;      /* H: tour of each HU (-1 = none) */
+    int16_t *su_tour;      /* S: tour of each SU (-1 = none) */
+    float *tour_cost_km;   /* T: per-tour cost C(g) (Table 2 row "C") */
+    float *tour_tcompl_h;  /* T: completion times (Table 2 row "T_compl") */
+    float *tour_twait_h;   /* T: average HU waiting times (Table 2 row "T_wait") */
+    int16_t *tour_n_hu;    /* T */
+    int16_t *tour_n_su;    /* T */
+    float cost_km;         /* C* (+inf if no feasible plan has been found) */
+    float tmax_h;          /* Tmax* */
+    uint32_t iter;         /* iterations run so far */
+} bl_plan;
+
+/* Search state of one instance (checkpoint / resume, host-driven loops).
+   Host buffers, caller-owned, sized from the instance. */
+typedef struct bl_state {
+    int16_t *xold_bp_order, *xold_tour_cnt, *xold_field_order, *xold_bp_cnt;
+    int16_t *xbest_bp_order, *xbest_tour_cnt, *xbest_field_order, *xbest_bp_cnt;
+    float cstar, tmaxstar;
+    uint32_t iter;
+} bl_state;
+
+typedef struct bl_handle bl_handle;
+
+/* Bytes of device workspace bl_plan_init_batch needs for these instances and
+   parameters (to pass a caller-owned buffer in bl_params.workspace). */
+int bl_workspace_bytes(const bl_instance *insts, int32_t n_inst, const bl_params *params, size_t *bytes);
+
+/* Algorithm 1, Steps 1-4 (Sec. 2.5): validate and copy the instance, build the
+   initial plan (nearest-neighbour BP chain cut into tours, fields to the
+   closest BP still short of its demand, nearest-neighbour field order from
+   the HQ), score it on the GPU (C*, Tmax*), set x_old = x* = x_init, and
+   prepare the kernels. `cuda_stream` is a cudaStream_t (NULL = default
+   stream); every later call on the handle is ordered on it. On success *out
+   owns all device memory (or uses params->workspace). Errors: BL_EINVAL,
+   BL_EINFEASIBLE_INSTANCE, BL_ETOO_LARGE, BL_ECUDA; *out is NULL then. */
+int bl_plan_init(const bl_instance *inst, const bl_params *params, void *cuda_stream, bl_handle **out);
+
+/* Same for n_inst independent instances of uneven size searched together:
+   one persistent launch per iteration covers all of them (work items ordered
+   largest instance first), each with its own x_old, x*, C*, Tmax* and
+   Philox counter word inst_idx+k. */
+int bl_plan_init_batch(const bl_instance *insts, int32_t n_inst, const bl_params *params, void *cuda_stream,
+                       bl_handle **out);
+
+/* Algorithm 1, Steps 5-16, n_iters times, asynchronously on the handle's
+   stream: per iteration the eps rule (Eq. 5), n_cand Philox moves and exact
+   scores per instance, the argmin (ties to the lowest index) and the update
+   of x_old, x*, C*, Tmax*. Launches are replayed from a CUDA graph. Device
+   errors (BL_ETIMEOUT) surface at the next synchronising call. */
+int bl_search_step(bl_handle *h, int32_t n_iters);
+
+/* Synchronise and report instance `inst`'s best plan x*, re-scored once for
+   the per-tour table (Table 2's rows). */
+int bl_best_plan(bl_handle *h, int32_t inst, bl_plan *out);
+
+/* Synchronise and copy instance `inst`'s search state to host buffers. */
+int bl_get_state(bl_handle *h, int32_t inst, bl_state *out);
+
+/* Replace instance `inst`'s search state (resume from a checkpoint). The plans
+   are validated; the copy is ordered on the handle's stream. */
+int bl_set_state(bl_handle *h, int32_t inst, const bl_state *in);
+
+/* Per-iteration log of instance `inst` for iterations [first, first+n) that
+   are still in the ring buffer: i*, C_{i*}, whether the base was x* (Eq. 5),
+   C* after the update, and the indicator of Fig. 3 (0 no improvement,
+   1 improved by a field move, 2 by a BP move). Host outputs, may be NULL. */
+int bl_get_log(bl_handle *h, int32_t inst, uint32_t first, int32_t n, int32_t *istar, float *c_istar,
+               int8_t *use_best, float *cstar, int8_t *indicator);
+
+/* Inspection: score candidates i0..i0+n-1 of iteration `iter` drawn from
+   base x* (use_best = 1) or x_old (0) of instance `inst`, without updating
+   anything; tmax_star is the gate's reference (pass the state's Tmax*).
+   Host outputs (any may be NULL): cost[n], tmax[n] (FP32; +inf when
+   infeasible), moves[n x 4] ({kind, vertex, a, b}: kind 0 field reinsert
+   (a = BP, b = slot), 1 BP reinsert (a = tour, b = slot), 2 field swap
+   (a = other field), 3 BP swap (a = other BP)), n_hu[n x T], n_su[n x T]. */
+int bl_score_candidates(bl_handle *h, int32_t inst, int32_t use_best, uint32_t iter, float tmax_star, int32_t i0,
+                        int32_t n, float *cost, float *tmax, int16_t *moves, int16_t *n_hu, int16_t *n_su);
+
+/* Inspection: the decoded candidate plans (Step 8 applied to the base) for
+   candidate indices idx[0..n-1]; plans is a host buffer of n x (2B+T+F)
+   int16, each row bp_order | tour_cnt | field_order | bp_cnt. */
+int bl_decode_candidates(bl_handle *h, int32_t inst, int32_t use_best, uint32_t iter, const int32_t *idx, int32_t n,
+                         int16_t *plans);
+
+/* Kernel configuration in use: threads per block, grid blocks, candidates
+   per work item, and the number of kernels one iteration launches. */
+int bl_get_config(bl_handle *h, int32_t *block_threads, int32_t *grid_blocks, int32_t *tile,
+                  int32_t *launches_per_iter);
+
+/* Release everything the handle owns. */
+int bl_plan_free(bl_handle *h);
+
+/* Message of the last failure on this handle ("" if none). */
+const char *bl_last_error(const bl_handle *h);
+
+/* Message of the last failure of a call that had no handle to report to. */
+const char *bl_global_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* BIOLOG_H */

@@ -995,14 +995,17 @@ typedef struct {
 } or_state;
 
 /* Algorithm 1, Steps 5-16 (GPU version), n candidates per iteration.
-   Per iteration outputs (each may be NULL): use_best, istar, c_istar, cstar,
-   tmaxstar, indicator (0 none, 1 improved by a field move, 2 by a BP move).
-   force_istar (may be NULL): when >= 0 at an iteration, that index is taken
-   as the argmin instead (used to follow another run through near-ties). */
+   Per iteration outputs (each may be NULL): use_best, istar (the argmin),
+   c_istar, cstar, tmaxstar, indicator (0 none, 1 improved by a field move,
+   2 by a BP move), margin of the argmin candidate, relative gap to the
+   second-best distinct cost. force_istar (may be NULL): when >= 0 at an
+   iteration, the search continues from that index instead of the argmin
+   (used to follow another run through near-ties); c_follow is the cost of
+   the index actually followed. */
 int or_search(const or_ctx *c, const or_params *prm, or_state *st, int32_t n_iters, int32_t n_cand,
               int32_t nthreads, int32_t *use_best_o, int32_t *istar_o, double *c_istar_o, double *cstar_o,
               double *tmaxstar_o, int32_t *indicator_o, double *margin_best_o, double *gap_o,
-              const int32_t *force_istar)
+              const int32_t *force_istar, double *c_follow_o)
 {
     const int T = c->T, B = c->B, F = c->F;
     oplan xold, xbest, base, cand;
@@ -1031,7 +1034,10 @@ int or_search(const or_ctx *c, const or_params *prm, or_state *st, int32_t n_ite
         double second = INFINITY;
         for (int32_t k = 0; k < n_cand; ++k) if (cost[k] != cost[istar] && cost[k] < second) second = cost[k];
         if (gap_o) gap_o[it] = (isfinite(cost[istar]) && isfinite(second)) ? (second - cost[istar]) / cost[istar] : INFINITY;
-        if (force_istar && force_istar[it] >= 0) istar = force_istar[it];
+        if (istar_o) istar_o[it] = istar;
+        if (c_istar_o) c_istar_o[it] = cost[istar];
+        if (force_istar && force_istar[it] >= 0 && force_istar[it] < n_cand) istar = force_istar[it];
+        if (c_follow_o) c_follow_o[it] = cost[istar];
         int ind = 0;
         int16_t mv[4];
         draw_move(c, prm, iter, (uint32_t)istar, &base, mv);
@@ -1050,8 +1056,6 @@ int or_search(const or_ctx *c, const or_params *prm, or_state *st, int32_t n_ite
             plan_copy(&xold, &base);
         }
         if (use_best_o) use_best_o[it] = use_best;
-        if (istar_o) istar_o[it] = istar;
-        if (c_istar_o) c_istar_o[it] = cost[istar];
         if (cstar_o) cstar_o[it] = st->cstar;
         if (tmaxstar_o) tmaxstar_o[it] = st->tmaxstar;
         if (indicator_o) indicator_o[it] = ind;

@@ -90,7 +90,7 @@ def lib():
             L.or_score_batch.argtypes = [C.c_void_p, C.POINTER(Params), C.c_uint32, i16p, i16p, i16p, i16p,
                                          C.c_double, C.c_int32, C.c_int32, C.c_int32, vp, vp, vp, vp, vp, vp, vp, vp]
             L.or_search.argtypes = [C.c_void_p, C.POINTER(Params), C.POINTER(_State), C.c_int32, C.c_int32, C.c_int32,
-                                    vp, vp, vp, vp, vp, vp, vp, vp, vp]
+                                    vp, vp, vp, vp, vp, vp, vp, vp, vp, vp]
             L.or_max_threads.restype = C.c_int
             _lib = L
     return _lib
@@ -246,17 +246,18 @@ class Oracle:
         use_best = np.zeros(n_iters, np.int32); istar = np.zeros(n_iters, np.int32)
         c_istar = np.zeros(n_iters); cstar = np.zeros(n_iters); tstar = np.zeros(n_iters)
         ind = np.zeros(n_iters, np.int32); mbest = np.zeros(n_iters); gap = np.zeros(n_iters)
+        follow = np.zeros(n_iters)
         force = None
         if force_istar is not None:
             force = np.ascontiguousarray(force_istar, dtype=np.int32)
         rc = lib().or_search(self._h, C.byref(params), C.byref(st), int(n_iters), int(n_cand), int(threads),
                              _p(use_best), _p(istar), _p(c_istar), _p(cstar), _p(tstar), _p(ind), _p(mbest), _p(gap),
-                             _p(force))
+                             _p(force), _p(follow))
         if rc:
             raise ValueError("bad state")
         state.cstar, state.tmaxstar, state.iter = st.cstar, st.tmaxstar, st.iter
         return dict(use_best=use_best.astype(bool), istar=istar, c_istar=c_istar, cstar=cstar, tmaxstar=tstar,
-                    indicator=ind, margin_best=mbest, gap=gap)
+                    indicator=ind, margin_best=mbest, gap=gap, c_follow=follow)
 
     def start(self, params: Params | None = None) -> "SearchState":
         """Algorithm 1, Step 4: x* = x_old = initial plan, C* and Tmax* from the scorer (no gate)."""

@@ -1,0 +1,64 @@
+"""The C-ABI library builds, loads and exports every entry point its header
+declares, and its host-side validation answers without a GPU."""
+import os
+import re
+
+import numpy as np
+import pytest
+
+from conftest import ROOT
+from paper_1909_10286_gb300 import biolog, build
+from paper_1909_10286_gb300 import instances as I
+
+
+@pytest.fixture(scope="module")
+def lib():
+    build.build()
+    return biolog.load()
+
+
+def _declared():
+    txt = open(os.path.join(ROOT, "include", "biolog.h")).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    return sorted(set(re.findall(r"\b(bl_[a-z_]+)\s*\(", txt)))
+
+
+def test_exports_every_declared_symbol(lib):
+    declared = _declared()
+    assert len(declared) >= 14
+    assert set(declared) == set(biolog.EXPORTS)
+    for name in declared:
+        assert hasattr(lib, name), name
+
+
+def test_workspace_query_and_validation_without_gpu(lib):
+    inst = I.make_instance("paper", 0)
+    p = biolog.make_params(n_cand=1 << 20)
+    assert biolog.workspace_bytes([inst], p) > 0
+    bad = I.make_instance("paper", 0)
+    bad.supply_t = bad.supply_t.copy(); bad.supply_t[3] = -1.0
+    with pytest.raises(biolog.BiologError) as e:
+        biolog.workspace_bytes([bad], p)
+    assert e.value.code == biolog.BL_EINVAL
+    infeas = I.make_instance("paper", 0)
+    infeas.demand_t = (infeas.demand_t * 2).astype(np.float32)
+    with pytest.raises(biolog.BiologError) as e:
+        biolog.workspace_bytes([infeas], p)
+    assert e.value.code == biolog.BL_EINFEASIBLE_INSTANCE
+    big = I.make_instance("large", 0)
+    big.n_tours = 17
+    with pytest.raises(biolog.BiologError) as e:
+        biolog.workspace_bytes([big], p)
+    assert e.value.code == biolog.BL_ETOO_LARGE
+    with pytest.raises(biolog.BiologError) as e:
+        biolog.workspace_bytes([inst], biolog.make_params(n_cand=0))
+    assert e.value.code == biolog.BL_EINVAL
+
+
+def test_no_cpu_fallback():
+    """Without a CUDA device the search refuses to run instead of falling back."""
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    with pytest.raises(biolog.BiologError):
+        biolog.plan_init(I.make_instance("tiny", 0), biolog.make_params(n_cand=64))
