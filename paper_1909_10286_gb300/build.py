@@ -43,6 +43,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
     tag = f"{os.getpid()}"
     cc = nvcc()
     common = ["-O3", "-std=c++17", "-Xcompiler", "-fPIC", "-I" + os.path.join(ROOT, "include")]
+    common += os.environ.get("BIOLOG_NVCC_FLAGS", "").split()   # e.g. tuning constants
     objs = [os.path.join(OUT, f"{os.path.splitext(s)[0]}.{tag}.o") for s in SOURCES]
     cmds = []
     for src, obj in zip(SOURCES, objs):

@@ -233,7 +233,9 @@ void build_blob(HostInst &h)
     L.off_hurq = take((size_t)H * 8);
     L.off_sufq = take((size_t)S * 8);
     L.off_sucq = take((size_t)S * 8);
-    L.off_suspd = take((size_t)S * 4);
+    L.off_suinv = take((size_t)S * 4);
+    L.off_sufill = take((size_t)S * 4);
+    L.off_rcp = take((size_t)(std::max(F, B) + 1) * 4);
     L.off_sugrp = take((size_t)S * 4);
     L.off_hudeal_m = take((size_t)T * T * 8);
     L.off_hudeal_q = take((size_t)T * T * 8);
@@ -250,14 +252,17 @@ void build_blob(HostInst &h)
     put(h.blob, L.off_supq, h.supq.m.data(), (size_t)F);
     put(h.blob, L.off_demq, h.demq.data(), (size_t)B);
     std::vector<long long> hurq((size_t)H), sufq((size_t)S), sucq((size_t)S);
-    std::vector<float> spd((size_t)S);
+    std::vector<float> inv_spd((size_t)S), fill_sorted((size_t)S);
+    std::vector<float> rcp((size_t)(std::max(F, B) + 1), 0.f);
+    for (size_t k = 1; k < rcp.size(); ++k) rcp[k] = (float)(1.0 / (double)k);
     std::vector<int32_t> grp((size_t)S), hu_id((size_t)H), su_id((size_t)S);
     for (int k = 0; k < H; ++k) { hurq[(size_t)k] = h.hurq.m[(size_t)h.hu_sorted[(size_t)k]]; hu_id[(size_t)k] = h.hu_sorted[(size_t)k]; }
     for (int k = 0; k < S; ++k) {
         const int s = h.su_sorted[(size_t)k];
         sufq[(size_t)k] = h.sufq.m[(size_t)s];
         sucq[(size_t)k] = h.sucq.m[(size_t)s];
-        spd[(size_t)k] = h.su_speed[(size_t)s];
+        inv_spd[(size_t)k] = (float)(1.0 / (double)h.su_speed[(size_t)s]);
+        fill_sorted[(size_t)k] = h.su_fill[(size_t)s];
         su_id[(size_t)k] = s;
         int g0 = k;
         while (g0 > 0 && h.su_fill[(size_t)h.su_sorted[(size_t)(g0 - 1)]] == h.su_fill[(size_t)s]) --g0;
@@ -266,7 +271,9 @@ void build_blob(HostInst &h)
     put(h.blob, L.off_hurq, hurq.data(), (size_t)H);
     put(h.blob, L.off_sufq, sufq.data(), (size_t)S);
     put(h.blob, L.off_sucq, sucq.data(), (size_t)S);
-    put(h.blob, L.off_suspd, spd.data(), (size_t)S);
+    put(h.blob, L.off_suinv, inv_spd.data(), (size_t)S);
+    put(h.blob, L.off_sufill, fill_sorted.data(), (size_t)S);
+    put(h.blob, L.off_rcp, rcp.data(), rcp.size());
     put(h.blob, L.off_sugrp, grp.data(), (size_t)S);
     put(h.blob, L.off_hu_id, hu_id.data(), (size_t)H);
     put(h.blob, L.off_su_id, su_id.data(), (size_t)S);
@@ -372,14 +379,20 @@ WsLayout layout_ws(const std::vector<HostInst> &insts, int n_work, int log_cap)
 
 int pick_shape(const std::vector<HostInst> &insts)
 {
-    int maxT = 0, maxS = 0, maxTotal = 0;
+    int maxT = 0, maxS = 0, maxH = 0, maxTotal = 0;
+    bool fits32 = true;   // unit sums of every instance fit in 31 bits
     for (const HostInst &h : insts) {
         maxT = std::max(maxT, h.T);
         maxS = std::max(maxS, h.S);
+        maxH = std::max(maxH, h.H);
         maxTotal = std::max(maxTotal, h.L.total_bytes);
+        long long a = 0, b = 0;
+        for (long long v : h.hurq.m) a += v;
+        for (long long v : h.sufq.m) b += v;
+        fits32 = fits32 && a < (1ll << 31) && b < (1ll << 31);
     }
-    if (maxS <= 64 && maxTotal <= kSmemDistLimit) {
-        if (maxT <= 4) return SHAPE_T4_S64_DSMEM;
+    if (maxS <= 64 && maxH <= 64 && maxTotal <= kSmemDistLimit) {
+        if (maxT <= 4 && maxS <= 32 && maxH <= 32 && fits32) return SHAPE_T4_S64_DSMEM;
         if (maxT <= 8) return SHAPE_T8_S64_DSMEM;
     }
     return SHAPE_T16_S128_GMEM;
@@ -517,7 +530,7 @@ int init_common(const bl_instance *insts, int32_t n_inst, const bl_params *param
     int maxT = 0;
     for (const HostInst &hi : h->insts) maxT = std::max(maxT, hi.T);
     for (const HostInst &hi : h->insts)
-        if (hi.T > max_tours_of(shape) || hi.S > max_su_of(shape)) {
+        if (hi.T > max_tours_of(shape) || hi.S > max_su_of(shape) || hi.H > (shape == SHAPE_T16_S128_GMEM ? 64 : max_su_of(shape))) {
             g_error = "no kernel shape fits";
             delete h;
             return BL_ETOO_LARGE;
@@ -592,6 +605,16 @@ int init_common(const bl_instance *insts, int32_t n_inst, const bl_params *param
         M.fq_scale = std::ldexp(1.0f, hi.sufq.exp);
         M.cq_scale = std::ldexp(1.0f, hi.sucq.exp);
         M.cq_scale_d = std::ldexp(1.0, hi.sucq.exp);
+        {
+            // shuttle distances in fixed point: quantum 2^(e-31) with e the exponent of the largest distance,
+            // so each rounded distance is < 2^31 and a tour's sum of n_f * d_f stays far below 2^63
+            float dmax = 0.f;
+            for (float d : hi.D) dmax = std::max(dmax, d);
+            int e = 0;
+            std::frexp((double)std::max(dmax, 1e-30f), &e);
+            M.dq_inv = std::ldexp(1.0f, 31 - e);
+            M.dq_scale = std::ldexp(1.0f, e - 31);
+        }
         M.L = hi.L;
         M.blob = h->at<unsigned char>(h->ws.blob[(size_t)i]);
         M.xold = h->at<int16_t>(h->ws.xold[(size_t)i]);

@@ -21,7 +21,9 @@ struct BlobLayout {
     int32_t off_hurq;      // i64[H]   HU rates, sorted by (rate, id), fixed point
     int32_t off_sufq;      // i64[S]   SU fill areas, sorted by (fill, id), fixed point
     int32_t off_sucq;      // i64[S]   SU capacities in the same sorted order, fixed point
-    int32_t off_suspd;     // f32[S]   SU speeds, same order
+    int32_t off_suinv;     // f32[S]   1 / SU speed, same order
+    int32_t off_sufill;    // f32[S]   SU fill areas (ha), same order
+    int32_t off_rcp;       // f32[R]   1/k for k = 0..R-1 (entry 0 unused), R = max(F, B) + 1
     int32_t off_sugrp;     // i32[S]   first sorted index with the same fill area
     int32_t off_hudeal_m;  // u64[T*T] HU masks of the round-robin dealing: [na-1][j]
     int32_t off_hudeal_q;  // i64[T*T] their fixed-point rate sums
@@ -48,6 +50,8 @@ struct InstMeta {
     float fq_scale;
     float cq_scale;
     double cq_scale_d;
+    float dq_inv;              // distances -> shuttle fixed point: round(d * dq_inv)
+    float dq_scale;            // and back: 2^k
     BlobLayout L;
     const unsigned char *blob; // device: this instance's table blob
     int16_t *xold;             // device: plan encodings (plan_len int16 each)
@@ -88,7 +92,7 @@ struct WorkItem {
 
 // Kernel shape class chosen per handle from the largest instance.
 enum ShapeClass : int32_t {
-    SHAPE_T4_S64_DSMEM = 0,   // tours <= 4,  SUs <= 64,  distances staged in shared memory
+    SHAPE_T4_S64_DSMEM = 0,   // tours <= 4,  HUs and SUs <= 32 (32-bit sets and sums), distances in shared memory
     SHAPE_T8_S64_DSMEM = 1,   // tours <= 8,  SUs <= 64,  distances staged in shared memory
     SHAPE_T16_S128_GMEM = 2,  // tours <= 16, SUs <= 128, distances read through L2
 };

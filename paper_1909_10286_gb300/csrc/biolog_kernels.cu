@@ -3,23 +3,29 @@
 // One launch = one iteration of Steps 6-16 for every instance of the handle:
 //   * each block stages an instance's tables (distances, supplies, fleet
 //     tables) into shared memory with one bulk asynchronous copy completed on
-//     an mbarrier, and loads the base plan chosen by the eps rule (Eq. 5);
-//   * for each candidate index i of its work item a thread draws the Step 8
-//     move from Philox4x32-10 with counter (i, iter, inst, 0), checks the
-//     Eq. 2 demands exactly in 64-bit fixed point and, if they hold, queues it;
-//   * queued candidates are scored one per thread: route aggregates traced as
-//     in Fig. 1, HU assignment and SU assignment by the local minimisation of
-//     Sec. 2.5 (Eq. 6, Algorithm 2), the path-length cost of Sec. 2.2 with the
-//     exact Eq. 4 ceiling, and the completion-time gate;
+//     an mbarrier, loads the base plan chosen by the eps rule (Eq. 5) and
+//     traces the base plan's tours once (route aggregates per tour);
+//   * every warp draws the Step 8 moves of 32 candidates at a time from
+//     Philox4x32-10 with counter (i, iter, inst, 0), checks the Eq. 2 demands
+//     exactly in 64-bit fixed point, and appends the feasible ones to its own
+//     queue; whenever 32 are queued, each lane scores one of them:
+//       - route aggregates of the tours the move touches, traced as in Fig. 1
+//         (the other tours reuse the base plan's aggregates: every per-tour
+//         value is a deterministic function of that tour's content, so the
+//         reuse is bit-identical to re-tracing);
+//       - HU assignment and SU assignment by the local minimisation of
+//         Sec. 2.5 (Eq. 6, Algorithm 2);
+//       - the path-length cost of Sec. 2.2 with the exact Eq. 4 ceiling, the
+//         shuttle sum in order-independent fixed point;
+//       - the completion-time gate;
 //   * a warp-shuffle + block argmin over keys (cost bits << 32 | i) gives one
 //     slot per work item; the block that finishes an instance's last work
 //     item reduces the slots, replays move i* on the base and updates x_old,
 //     x*, C*, Tmax* (Steps 13-16).
-// Per-tour state of a candidate lives in shared memory, one column per thread.
-// Every per-tour value is a deterministic function of that tour's content
-// (sequential sums in tour order, fixed-point unit sums, explicitly rounded FP
-// operations), so identical tours give bit-identical times in every candidate.
+// Per-tour state of a candidate lives in registers (up to 4 tours) or in
+// shared memory, one column per thread (more tours).
 #include <cstdint>
+#include <type_traits>
 #include <cuda_runtime.h>
 
 #include "biolog_internal.h"
@@ -105,23 +111,48 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity
 // ---------------------------------------------------------------------------
 // Shapes
 // ---------------------------------------------------------------------------
-template <int MAXT_, int SW_, bool DSM_, int NT_>
+// MAXT tours; SW 64-bit words per SU set (SW = 0: one 32-bit word, with
+// 32-bit fixed-point unit sums); distances in shared memory or read through
+// L2; NT threads per block (a compile-time constant: per-tour state offsets
+// become immediates); MINB resident blocks per SM the register budget targets.
+template <int MAXT_, int SW_, bool DSM_, int NT_, int MINB_>
 struct Shape {
-    static constexpr int MAXT = MAXT_;   // tours
-    static constexpr int SW = SW_;       // 64-bit words of an SU set
-    static constexpr bool DSM = DSM_;    // distances in shared memory
-    static constexpr int NT = NT_;       // threads per block (compile time: per-tour state offsets are immediates)
+    static constexpr int MAXT = MAXT_;
+    static constexpr int SW = SW_;
+    static constexpr bool DSM = DSM_;
+    static constexpr int NT = NT_;
+    static constexpr int MINB = MINB_;
+    using Mask = typename std::conditional<SW_ == 0, uint32_t, unsigned long long>::type;
+    using Sum = typename std::conditional<SW_ == 0, int32_t, long long>::type;
+    static constexpr int WORDS = SW_ == 0 ? 1 : SW_;
 };
 
-using ShapeA = Shape<4, 1, true, 256>;
-using ShapeB = Shape<8, 1, true, 128>;
-using ShapeC = Shape<16, 2, false, 128>;
+#ifndef BIOLOG_SHAPEA_MINB
+#define BIOLOG_SHAPEA_MINB 2
+#endif
+using ShapeA = Shape<4, 0, true, 256, BIOLOG_SHAPEA_MINB>;   // <= 4 tours, <= 32 HUs/SUs, 32-bit sums
+using ShapeB = Shape<8, 1, true, 128, 4>;                     // <= 8 tours, <= 64 HUs/SUs
+using ShapeC = Shape<16, 2, false, 128, 2>;                   // <= 16 tours, <= 128 SUs, distances via L2
 
-constexpr int NFLT = 7;   // per-tour floats: LHU, LSU, A, DB2 (2 Dbar), Tc, Tw, Rf
-constexpr int F_LHU = 0, F_LSU = 1, F_A = 2, F_DB2 = 3, F_TC = 4, F_TW = 5, F_RF = 6;
-constexpr int NI64 = 2;   // per-tour int64: HU rate sum, SU fill sum (fixed point)
-constexpr int Q_RQ = 0, Q_SAQ = 1;
-constexpr int QUEUE_PER_THREAD = 2;
+constexpr int NF32 = 7;   // per-tour floats: LHU, LSU, A, DB2 (2 Dbar), Tc, Tw, 1/R
+constexpr int WQ = 64;    // per-warp queue of feasible candidates (ring buffer)
+
+template <typename M>
+__device__ __forceinline__ int popc_m(M m) { if constexpr (sizeof(M) == 4) return __popc(m); else return __popcll(m); }
+template <typename M>
+__device__ __forceinline__ int ffs_m(M m) { if constexpr (sizeof(M) == 4) return __ffs((int)m) - 1; else return __ffsll((long long)m) - 1; }
+template <typename M>
+__device__ __forceinline__ int hibit_m(M m) { if constexpr (sizeof(M) == 4) return 31 - __clz((int)m); else return 63 - __clzll((long long)m); }
+template <typename S>
+__device__ __forceinline__ float to_f(S v) { if constexpr (sizeof(S) == 4) return __int2float_rn(v); else return __ll2float_rn(v); }
+
+// A per-tour value of the calling thread: a shared-memory column.
+template <typename T, int NT>
+struct Col {
+    T *p;
+    __device__ __forceinline__ T get(int g) const { return p[g * NT]; }
+    __device__ __forceinline__ void set(int g, T v) { p[g * NT] = v; }
+};
 
 // Instance tables and base plan as seen by one block.
 struct Ctx {
@@ -129,18 +160,19 @@ struct Ctx {
     const float *D;
     const float *area, *supply;
     const long long *supq, *demq, *hurq, *sufq, *sucq;
-    const float *suspd;
+    const float *suinv, *sufill, *rcp;
     const int *sugrp;
     const unsigned long long *hudeal_m, *sudeal_m;
     const long long *hudeal_q, *sudeal_q;
     const int *hu_id, *su_id;
-    float inv_v, rqs, fqs, cqs;
+    float inv_v, rqs, fqs, cqs, dq_inv, dq_scale;
     double cqs_d;
     // base plan and derived tables (shared memory)
     const int16_t *bp_order, *tour_cnt, *field_order, *bp_cnt;
     const int16_t *tour_start, *bp_start, *field_bp, *field_pos, *bp_tour, *bp_pos;
     const long long *base_supq;
     const int8_t *bad;
+    const float *bLHU, *bLSU, *bA, *bDB2;   // base plan's route aggregates per tour
     int nbad;
     __device__ __forceinline__ float d(int i, int j) const { return D[i * N + j]; }
 };
@@ -230,7 +262,75 @@ struct View {
         if (kind == 2) f = (f == v) ? w : (f == w ? v : f);
         return f;
     }
+    // tour of BP b in the candidate
+    __device__ __forceinline__ int tour_of_bp(const Ctx &c, int b) const
+    {
+        if (kind == 1 && b == v) return dg;
+        if (kind == 3) {
+            if (b == v) return c.bp_tour[w];
+            if (b == w) return c.bp_tour[v];
+        }
+        return c.bp_tour[b];
+    }
+    // BP of field f in the candidate
+    __device__ __forceinline__ int bp_of_field(const Ctx &c, int f) const
+    {
+        if (kind == 0 && f == v) return dg;
+        if (kind == 2) {
+            if (f == v) return c.field_bp[w];
+            if (f == w) return c.field_bp[v];
+        }
+        return c.field_bp[f];
+    }
+    // tours whose field sequence differs from the base plan (bit mask)
+    __device__ __forceinline__ unsigned touched(const Ctx &c) const
+    {
+        switch (kind) {
+        case 0: return (1u << c.bp_tour[sg]) | (1u << c.bp_tour[dg]);
+        case 1: return (1u << sg) | (1u << dg);
+        case 2: return (1u << c.bp_tour[c.field_bp[v]]) | (1u << c.bp_tour[c.field_bp[w]]);
+        case 3: return (1u << c.bp_tour[v]) | (1u << c.bp_tour[w]);
+        default: return 0u;
+        }
+    }
 };
+
+// Route aggregates of tour g as in Fig. 1 (Sec. 2.2): HU route through the
+// fields in order, SU repositioning route, harvested area, and 2x the mean of
+// per-BP mean field-to-BP distances (Algorithm 2, Step 1). Sequential FP32
+// sums in plan order.
+struct TourAgg {
+    float LHU, LSU, A, DB2;
+};
+
+__device__ __forceinline__ TourAgg trace_tour(const Ctx &c, const View &x, int g, int nb)
+{
+    int prevF = 0, anchor = 0;
+    float LHU = 0.f, LSU = 0.f, A = 0.f, Dsum = 0.f;
+    for (int j = 0; j < nb; ++j) {
+        const int b = x.bp_at(c, g, j);
+        const int nf = x.bp_len(c, b);
+        const int bn = 1 + b;
+        float Sb = 0.f;
+        for (int k = 0; k < nf; ++k) {
+            const int f = x.field_at(c, b, k);
+            const int fn = 1 + c.B + f;
+            LHU = __fadd_rn(LHU, c.d(prevF, fn));
+            if (k == 0) LSU = __fadd_rn(LSU, c.d(anchor, fn));
+            A = __fadd_rn(A, c.area[f]);
+            Sb = __fadd_rn(Sb, c.d(fn, bn));
+            prevF = fn;
+        }
+        Dsum = __fadd_rn(Dsum, __fmul_rn(Sb, c.rcp[nf]));
+        anchor = bn;
+    }
+    TourAgg t;
+    t.LHU = __fadd_rn(LHU, c.d(prevF, 0));
+    t.LSU = __fadd_rn(LSU, c.d(anchor, 0));
+    t.A = A;
+    t.DB2 = __fmul_rn(2.0f, __fmul_rn(Dsum, c.rcp[nb]));
+    return t;
+}
 
 // Eq. 2 for the candidate, exactly: only the BPs whose field set changed are
 // re-summed; the others keep the base's status.
@@ -253,8 +353,9 @@ __device__ __forceinline__ bool demand_ok(const Ctx &c, const MoveRec &m)
     return c.nbad == 0;
 }
 
-// smallest k with k * cap >= s * nsu, exactly, near an integer hint (FP64 on a
-// rare path; a - p is exact by Sterbenz since p is within 1e-6 of a)
+// Eq. 4: n = ceil(s * nsu / cap). FP32 fast path; within 2^-21 of an integer the
+// smallest k with k * cap >= s * nsu is found exactly in FP64 (a - p is exact
+// by Sterbenz since p is within 1e-6 of a; k*cap = p + e exactly by FMA).
 __device__ __noinline__ int exact_ceil(float s, int nsu, double cap, float q)
 {
     const double a = (double)s * (double)nsu;
@@ -265,38 +366,88 @@ __device__ __noinline__ int exact_ceil(float s, int nsu, double cap, float q)
     return (dlt > e) ? (int)k + 1 : (int)k;
 }
 
-__device__ __forceinline__ int popc_su(const unsigned long long *w, int SW)
+// Critical SU of a set (Eq. 6 reading): largest fill area, ties to the lowest
+// id = the first member of the highest tie group in sorted order. m1 is the
+// second 64-bit word (sets of more than 64 SUs only).
+template <class SH>
+__device__ __forceinline__ int su_star(const Ctx &c, typename SH::Mask m0, unsigned long long m1)
 {
-    int n = __popcll(w[0]);
-    if (SW > 1) n += __popcll(w[1]);
-    return n;
+    using M = typename SH::Mask;
+    int hb;
+    if (SH::SW > 1 && m1) hb = 64 + hibit_m(m1);
+    else hb = hibit_m(m0);
+    const int grp = c.sugrp[hb];
+    if (SH::SW > 1 && grp >= 64) return 64 + ffs_m(m1 & (~0ull << (grp - 64)));
+    const M lo = m0 & (M)(~(M)0 << grp);
+    if (lo) return ffs_m(lo);
+    return 64 + ffs_m(m1);
 }
 
-// Per-candidate scoring. Tour state: tf[(field*MAXT+g)*nt + tid], etc.
+template <class SH>
+__device__ __forceinline__ long long cap_sum(const Ctx &c, typename SH::Mask s0, unsigned long long s1)
+{
+    long long q = 0;
+    while (s0) { const int k = ffs_m(s0); s0 &= s0 - 1; q += c.sucq[k]; }
+    if (SH::SW > 1)
+        while (s1) { const int k = ffs_m(s1); s1 &= s1 - 1; q += c.sucq[64 + k]; }
+    return q;
+}
+
 struct ScoreOut {
     float cost, tmax;
 };
 
+// Per-thread per-tour state: one shared-memory column per value.
+template <class SH>
+struct TourState {
+    static constexpr int MAXT = SH::MAXT, NT = SH::NT;
+    using M = typename SH::Mask;
+    using S = typename SH::Sum;
+    Col<float, NT> LHU, LSU, A, DB2, Tc, Tw, iR;
+    Col<int, NT> star;
+    Col<S, NT> Rq, Saq;
+    Col<M, NT> Hm, S0;
+    Col<unsigned long long, NT> S1, Sh;
+    __device__ __forceinline__ void bind(unsigned char *base, int tid)
+    {
+        constexpr int C = MAXT * NT;
+        float *f = (float *)base + tid;
+        LHU.p = f; LSU.p = f + C; A.p = f + 2 * C; DB2.p = f + 3 * C; Tc.p = f + 4 * C; Tw.p = f + 5 * C;
+        iR.p = f + 6 * C;
+        int *i = (int *)base + (size_t)NF32 * C + tid;
+        star.p = i;
+        S *q = (S *)((int *)base + (size_t)(NF32 + 1) * C) + tid;
+        Rq.p = q; Saq.p = q + C;
+        M *m = (M *)((S *)((int *)base + (size_t)(NF32 + 1) * C) + 2 * C) + tid;
+        Hm.p = m; S0.p = m + C;
+        unsigned long long *w = (unsigned long long *)((M *)((S *)((int *)base + (size_t)(NF32 + 1) * C) + 2 * C) + 2 * C) + tid;
+        S1.p = w; Sh.p = w + C;
+    }
+    static constexpr size_t bytes()
+    {
+        constexpr size_t C = (size_t)MAXT * NT;
+        return (NF32 + 1) * C * 4 + 2 * C * sizeof(S) + 2 * C * sizeof(M) + 2 * C * 8;
+    }
+};
+
+// Per-candidate scoring.
 template <class SH, bool DUMP>
 __device__ ScoreOut score_candidate(const Ctx &c, const SearchParams &p, const MoveRec &m, float tmax_star,
-                                    float *tf, long long *tq, unsigned long long *tm, int nt, int tid,
-                                    int16_t *o_nhu, int16_t *o_nsu, float *o_tc, float *o_tw, float *o_tcost,
-                                    int16_t *o_hu, int16_t *o_su)
+                                    unsigned char *tstate, int tid, int16_t *o_nhu, int16_t *o_nsu, float *o_tc,
+                                    float *o_tw, float *o_tcost, int16_t *o_hu, int16_t *o_su)
 {
-    constexpr int MAXT = SH::MAXT, SW = SH::SW, NT = SH::NT;
-    (void)nt;
-    tf += tid; tq += tid; tm += tid;
-#define TF(fld, g) tf[((fld) * MAXT + (g)) * NT]
-#define TQ(fld, g) tq[((fld) * MAXT + (g)) * NT]
-#define TM(fld, g) tm[((fld) * MAXT + (g)) * NT]
+    constexpr int MAXT = SH::MAXT, SW = SH::SW;
+    using M = typename SH::Mask;
+    using S = typename SH::Sum;
+    TourState<SH> ts;
+    ts.bind(tstate, tid);
 #define FOR_ACTIVE(g) _Pragma("unroll") for (int g = 0; g < MAXT; ++g) if ((amask >> g) & 1u)
     ScoreOut out;
-    out.cost = __int_as_float(0x7f800000);
-    out.tmax = __int_as_float(0x7f800000);
     View x;
     x.set(c, m);
 
-    // --- route aggregates (Fig. 1, Sec. 2.2)
+    // --- route aggregates (Fig. 1, Sec. 2.2): trace the touched tours, reuse the base's
+    const unsigned touched = x.touched(c);
     unsigned amask = 0;
     int na = 0;
     for (int g = 0; g < c.T; ++g) {
@@ -304,237 +455,273 @@ __device__ ScoreOut score_candidate(const Ctx &c, const SearchParams &p, const M
         if (nb == 0) continue;
         amask |= 1u << g;
         ++na;
-        int prevF = 0, anchor = 0;
-        float LHU = 0.f, LSU = 0.f, A = 0.f, Dsum = 0.f;
-        for (int j = 0; j < nb; ++j) {
-            const int b = x.bp_at(c, g, j);
-            const int nf = x.bp_len(c, b);
-            const int bn = 1 + b;
-            float Sb = 0.f;
-            for (int k = 0; k < nf; ++k) {
-                const int f = x.field_at(c, b, k);
-                const int fn = 1 + c.B + f;
-                LHU = __fadd_rn(LHU, c.d(prevF, fn));
-                if (k == 0) LSU = __fadd_rn(LSU, c.d(anchor, fn));
-                A = __fadd_rn(A, c.area[f]);
-                Sb = __fadd_rn(Sb, c.d(fn, bn));
-                prevF = fn;
-            }
-            Dsum = __fadd_rn(Dsum, __fdiv_rn(Sb, (float)nf));
-            anchor = bn;
-        }
-        LHU = __fadd_rn(LHU, c.d(prevF, 0));
-        LSU = __fadd_rn(LSU, c.d(anchor, 0));
-        TF(F_LHU, g) = LHU;
-        TF(F_LSU, g) = LSU;
-        TF(F_A, g) = A;
-        TF(F_DB2, g) = __fmul_rn(2.0f, __fdiv_rn(Dsum, (float)nb));
+        TourAgg t;
+        if ((touched >> g) & 1u) t = trace_tour(c, x, g, nb);
+        else { t.LHU = c.bLHU[g]; t.LSU = c.bLSU[g]; t.A = c.bA[g]; t.DB2 = c.bDB2[g]; }
+        ts.LHU.set(g, t.LHU); ts.LSU.set(g, t.LSU); ts.A.set(g, t.A); ts.DB2.set(g, t.DB2);
     }
-
-    // --- HU assignment (Sec. 2.5): round-robin dealing, then Algorithm 2 on T_compl
     const int di = (na - 1) * c.T;
     const int g_first = __ffs(amask) - 1;
+
+    // --- HU assignment (Sec. 2.5): round-robin dealing, then Algorithm 2 on T_compl
+    float tv[MAXT];   // the round's times, in registers for the picks
     {
-    int j = 0;
-    FOR_ACTIVE(g) {
-        TM(0, g) = c.hudeal_m[di + j];
-        const long long rq = c.hudeal_q[di + j];
-        TQ(Q_RQ, g) = rq;
-        const float R = __fmul_rn(__ll2float_rn(rq), c.rqs);
-        TF(F_RF, g) = R;
-        TF(F_TC, g) = __fmaf_rn(TF(F_LHU, g), c.inv_v, __fdiv_rn(TF(F_A, g), R));
-        ++j;
-    }
+        int j = 0;
+        FOR_ACTIVE(g) {
+            ts.Hm.set(g, (M)c.hudeal_m[di + j]);
+            const S rq = (S)c.hudeal_q[di + j];
+            ts.Rq.set(g, rq);
+            const float R = __fmul_rn(to_f(rq), c.rqs);
+            const float t = __fmaf_rn(ts.LHU.get(g), c.inv_v, __fdividef(ts.A.get(g), R));
+            ts.Tc.set(g, t);
+            tv[g] = t;
+            ++j;
+        }
     }
     if (!p.fix_resources && na >= 2) {
         for (int round = 0; round < c.H; ++round) {
             int gx = g_first, gx2 = -1, gn = -1;
-            FOR_ACTIVE(g) if (TF(F_TC, g) > TF(F_TC, gx)) gx = g;
-            FOR_ACTIVE(g) if (g != gx && (gx2 < 0 || TF(F_TC, g) > TF(F_TC, gx2))) gx2 = g;
-            if (na == 2) gn = gx2;
-            else
-                FOR_ACTIVE(g) if (g != gx && g != gx2 && (gn < 0 || TF(F_TC, g) < TF(F_TC, gn))) gn = g;
-            const unsigned long long mn = TM(0, gn);
-            if (__popcll(mn) <= 1) break;
-            const float old_max = TF(F_TC, gx);
-            const int last = 63 - __clzll((long long)mn);
-            const float ref2 = TF(F_TC, gx2);
-            const float Lx = TF(F_LHU, gx), Ax = TF(F_A, gx), Ln = TF(F_LHU, gn), An = TF(F_A, gn);
-            const long long rqx = TQ(Q_RQ, gx), rqn = TQ(Q_RQ, gn);
-            unsigned long long mm = mn;
+            float tx = 0.f, tx2 = 0.f, tn = 0.f;
+#pragma unroll
+            for (int g = 0; g < MAXT; ++g)
+                if (((amask >> g) & 1u) && g == g_first) tx = tv[g];
+            FOR_ACTIVE(g) if (tv[g] > tx) { tx = tv[g]; gx = g; }
+            FOR_ACTIVE(g) if (g != gx && (gx2 < 0 || tv[g] > tx2)) { tx2 = tv[g]; gx2 = g; }
+            if (na == 2) { gn = gx2; tn = tx2; }
+            else FOR_ACTIVE(g) if (g != gx && g != gx2 && (gn < 0 || tv[g] < tn)) { tn = tv[g]; gn = g; }
+            const M mn = ts.Hm.get(gn);
+            if (popc_m(mn) <= 1) break;
+            const int last = hibit_m(mn);
+            const float Lx = ts.LHU.get(gx), Ax = ts.A.get(gx), Ln = ts.LHU.get(gn), An = ts.A.get(gn);
+            const S rqx = ts.Rq.get(gx), rqn = ts.Rq.get(gn);
+            M mm = mn;
             int k = -1;
-            float tmx = 0.f, tmn = 0.f, Rx = 0.f, Rn = 0.f;
-            long long nqx = 0, nqn = 0;
+            float tmx = 0.f, tmn = 0.f;
+            S nqx = 0, nqn = 0;
             while (mm) {
-                k = __ffsll((long long)mm) - 1;
+                k = ffs_m(mm);
                 mm &= mm - 1;
-                nqx = rqx + c.hurq[k];
-                nqn = rqn - c.hurq[k];
-                Rx = __fmul_rn(__ll2float_rn(nqx), c.rqs);
-                Rn = __fmul_rn(__ll2float_rn(nqn), c.rqs);
-                tmx = __fmaf_rn(Lx, c.inv_v, __fdiv_rn(Ax, Rx));
-                tmn = __fmaf_rn(Ln, c.inv_v, __fdiv_rn(An, Rn));
-                const float ref = (na == 2) ? tmn : ref2;
+                nqx = rqx + (S)c.hurq[k];
+                nqn = rqn - (S)c.hurq[k];
+                tmx = __fmaf_rn(Lx, c.inv_v, __fdividef(Ax, __fmul_rn(to_f(nqx), c.rqs)));
+                tmn = __fmaf_rn(Ln, c.inv_v, __fdividef(An, __fmul_rn(to_f(nqn), c.rqs)));
+                const float ref = (na == 2) ? tmn : tx2;
                 if (tmx < ref || k == last) break;
             }
             float nm = (tmx > tmn) ? tmx : tmn;
-            FOR_ACTIVE(g) if (g != gx && g != gn && TF(F_TC, g) > nm) nm = TF(F_TC, g);
-            if (!(nm < old_max)) break;   // the accepted move does not lower the maximum: keep the old state
-            const unsigned long long bit = 1ull << k;
-            TM(0, gx) |= bit;
-            TM(0, gn) &= ~bit;
-            TQ(Q_RQ, gx) = nqx; TQ(Q_RQ, gn) = nqn;
-            TF(F_RF, gx) = Rx; TF(F_RF, gn) = Rn;
-            TF(F_TC, gx) = tmx; TF(F_TC, gn) = tmn;
-        }
-    }
-    float tmax = TF(F_TC, g_first);
-    FOR_ACTIVE(g) tmax = fmaxf(tmax, TF(F_TC, g));
-
-    // --- SU assignment (Algorithm 2, Eq. 6)
-    {
-    int j = 0;
-    FOR_ACTIVE(g) {
+            FOR_ACTIVE(g) if (g != gx && g != gn && tv[g] > nm) nm = tv[g];
+            if (!(nm < tx)) break;   // the accepted move does not lower the maximum: keep the old state
+            const M bit = (M)1 << k;
+            ts.Hm.set(gx, ts.Hm.get(gx) | bit);
+            ts.Hm.set(gn, mn & ~bit);
+            ts.Rq.set(gx, nqx); ts.Rq.set(gn, nqn);
+            ts.Tc.set(gx, tmx); ts.Tc.set(gn, tmn);
 #pragma unroll
-        for (int w = 0; w < SW; ++w) TM(1 + w, g) = c.sudeal_m[(di + j) * 2 + w];
-        TQ(Q_SAQ, g) = c.sudeal_q[di + j];
-        ++j;
-    }
-    }
-    // T_wait of tour g with SU set `ms` and fill sum `saq`
-    auto twait = [&](int g, const unsigned long long *ms, long long saq) -> float {
-        int hb;
-        if (SW > 1 && ms[1]) hb = 64 + 63 - __clzll((long long)ms[1]);
-        else hb = 63 - __clzll((long long)ms[0]);
-        const int grp = c.sugrp[hb];
-        int star;
-        if (SW > 1 && grp >= 64) {
-            star = 64 + __ffsll((long long)(ms[1] & (~0ull << (grp - 64)))) - 1;
-        } else {
-            const unsigned long long lo = ms[0] & (~0ull << grp);
-            if (lo) star = __ffsll((long long)lo) - 1;
-            else star = 64 + __ffsll((long long)ms[1]) - 1;
+            for (int g = 0; g < MAXT; ++g) tv[g] = (g == gx) ? tmx : ((g == gn) ? tmn : tv[g]);
         }
-        const float fill = __fmul_rn(__ll2float_rn(saq - c.sufq[star]), c.fqs);
-        return __fsub_rn(__fdiv_rn(TF(F_DB2, g), c.suspd[star]), __fdiv_rn(fill, TF(F_RF, g)));
-    };
-    FOR_ACTIVE(g) {
-        unsigned long long ms[2] = {TM(1, g), SW > 1 ? TM(2, g) : 0ull};
-        TF(F_TW, g) = twait(g, ms, TQ(Q_SAQ, g));
+    }
+    float tmax = tv[0];
+    {
+        bool first = true;
+        FOR_ACTIVE(g) { tmax = first ? tv[g] : fmaxf(tmax, tv[g]); first = false; }
+    }
+
+    // --- SU assignment (Algorithm 2, Eq. 6). R(g) is fixed now: one reciprocal per tour.
+    {
+        int j = 0;
+        FOR_ACTIVE(g) {
+            const M m0 = (M)c.sudeal_m[(di + j) * 2];
+            const unsigned long long m1 = (SW > 1) ? c.sudeal_m[(di + j) * 2 + 1] : 0ull;
+            ts.S0.set(g, m0);
+            if (SW > 1) ts.S1.set(g, m1);
+            const S sq = (S)c.sudeal_q[di + j];
+            ts.Saq.set(g, sq);
+            const float ir = __fdividef(1.0f, __fmul_rn(to_f(ts.Rq.get(g)), c.rqs));
+            ts.iR.set(g, ir);
+            const int st = su_star<SH>(c, m0, m1);
+            ts.star.set(g, st);
+            const float fill = __fmul_rn(to_f((S)(sq - (S)c.sufq[st])), c.fqs);
+            const float t = __fmaf_rn(-fill, ir, __fmul_rn(ts.DB2.get(g), c.suinv[st]));
+            ts.Tw.set(g, t);
+            tv[g] = t;
+            ++j;
+        }
     }
     if (!p.fix_resources && na >= 2) {
         for (int round = 0; round < c.S; ++round) {
             int gx = g_first, gx2 = -1, gn = -1;
-            FOR_ACTIVE(g) if (TF(F_TW, g) > TF(F_TW, gx)) gx = g;
-            FOR_ACTIVE(g) if (g != gx && (gx2 < 0 || TF(F_TW, g) > TF(F_TW, gx2))) gx2 = g;
-            if (na == 2) gn = gx2;
-            else
-                FOR_ACTIVE(g) if (g != gx && g != gx2 && (gn < 0 || TF(F_TW, g) < TF(F_TW, gn))) gn = g;
-            unsigned long long mn[2] = {TM(1, gn), SW > 1 ? TM(2, gn) : 0ull};
-            if (popc_su(mn, SW) <= 1) break;
-            unsigned long long mx[2] = {TM(1, gx), SW > 1 ? TM(2, gx) : 0ull};
-            const float old_max = TF(F_TW, gx);
-            int last;
-            if (SW > 1 && mn[1]) last = 64 + 63 - __clzll((long long)mn[1]);
-            else last = 63 - __clzll((long long)mn[0]);
-            const float ref2 = TF(F_TW, gx2);
-            const long long sqx = TQ(Q_SAQ, gx), sqn = TQ(Q_SAQ, gn);
-            unsigned long long rest[2] = {mn[0], mn[1]};
-            int k = -1;
+            float tx = 0.f, tx2 = 0.f, tn = 0.f;
+#pragma unroll
+            for (int g = 0; g < MAXT; ++g)
+                if (((amask >> g) & 1u) && g == g_first) tx = tv[g];
+            FOR_ACTIVE(g) if (tv[g] > tx) { tx = tv[g]; gx = g; }
+            FOR_ACTIVE(g) if (g != gx && (gx2 < 0 || tv[g] > tx2)) { tx2 = tv[g]; gx2 = g; }
+            if (na == 2) { gn = gx2; tn = tx2; }
+            else FOR_ACTIVE(g) if (g != gx && g != gx2 && (gn < 0 || tv[g] < tn)) { tn = tv[g]; gn = g; }
+            const M n0 = ts.S0.get(gn);
+            const unsigned long long n1 = (SW > 1) ? ts.S1.get(gn) : 0ull;
+            if (popc_m(n0) + (SW > 1 ? popc_m(n1) : 0) <= 1) break;
+            const int last = (SW > 1 && n1) ? 64 + hibit_m(n1) : hibit_m(n0);
+            const int star_x = ts.star.get(gx), grp_x = c.sugrp[star_x];
+            const int star_n = ts.star.get(gn);
+            const S sqx = ts.Saq.get(gx), sqn = ts.Saq.get(gn);
+            const float DBx = ts.DB2.get(gx), DBn = ts.DB2.get(gn), iRx = ts.iR.get(gx), iRn = ts.iR.get(gn);
+            M r0 = n0;
+            unsigned long long r1 = n1;
+            int k = -1, sx = star_x, sn = star_n;
             float tmx = 0.f, tmn = 0.f;
-            long long nqx = 0, nqn = 0;
-            unsigned long long ax[2], an[2];
-            while (rest[0] | (SW > 1 ? rest[1] : 0ull)) {
-                if (rest[0]) { k = __ffsll((long long)rest[0]) - 1; rest[0] &= rest[0] - 1; }
-                else { k = 64 + __ffsll((long long)rest[1]) - 1; rest[1] &= rest[1] - 1; }
-                ax[0] = mx[0]; an[0] = mn[0];
-                ax[1] = mx[1]; an[1] = mn[1];
-                if (k < 64) { ax[0] |= 1ull << k; an[0] &= ~(1ull << k); }
-                else { ax[1] |= 1ull << (k - 64); an[1] &= ~(1ull << (k - 64)); }
-                nqx = sqx + c.sufq[k];
-                nqn = sqn - c.sufq[k];
-                tmx = twait(gx, ax, nqx);
-                tmn = twait(gn, an, nqn);
-                const float ref = (na == 2) ? tmn : ref2;
+            while (r0 | (SW > 1 ? r1 : 0ull)) {
+                if (r0) { k = ffs_m(r0); r0 &= r0 - 1; }
+                else { k = 64 + ffs_m(r1); r1 &= r1 - 1; }
+                const float ak = c.sufill[k];
+                // g_max gains SU k. Unless k becomes its critical SU (a higher tie group, or the
+                // same group at a lower position), one more SU fills during the critical round
+                // trip: T_wait drops by a_k / R(g_max) (Eq. 6).
+                const int gk = c.sugrp[k];
+                if (gk > grp_x || (gk == grp_x && k < star_x)) {
+                    sx = k;
+                    tmx = __fmaf_rn(-__fmul_rn(to_f(sqx), c.fqs), iRx, __fmul_rn(DBx, c.suinv[k]));
+                } else {
+                    sx = star_x;
+                    tmx = __fmaf_rn(-ak, iRx, tx);
+                }
+                // g_min loses SU k: T_wait rises by a_k / R(g_min), unless k was its critical SU
+                if (k != star_n) {
+                    sn = star_n;
+                    tmn = __fmaf_rn(ak, iRn, tn);
+                } else {
+                    M b0 = n0;
+                    unsigned long long b1 = n1;
+                    if (k < 64) b0 &= ~((M)1 << k); else b1 &= ~(1ull << (k - 64));
+                    sn = su_star<SH>(c, b0, b1);
+                    tmn = __fmaf_rn(-__fmul_rn(to_f((S)(sqn - (S)c.sufq[k] - (S)c.sufq[sn])), c.fqs), iRn,
+                                    __fmul_rn(DBn, c.suinv[sn]));
+                }
+                const float ref = (na == 2) ? tmn : tx2;
                 if (tmx < ref || k == last) break;
             }
             float nm = (tmx > tmn) ? tmx : tmn;
-            FOR_ACTIVE(g) if (g != gx && g != gn && TF(F_TW, g) > nm) nm = TF(F_TW, g);
-            if (!(nm < old_max)) break;
-            TM(1, gx) = ax[0]; TM(1, gn) = an[0];
-            if (SW > 1) { TM(2, gx) = ax[1]; TM(2, gn) = an[1]; }
-            TQ(Q_SAQ, gx) = nqx; TQ(Q_SAQ, gn) = nqn;
-            TF(F_TW, gx) = tmx; TF(F_TW, gn) = tmn;
+            FOR_ACTIVE(g) if (g != gx && g != gn && tv[g] > nm) nm = tv[g];
+            if (!(nm < tx)) break;
+            if (k < 64) {
+                const M bit = (M)1 << k;
+                ts.S0.set(gx, ts.S0.get(gx) | bit);
+                ts.S0.set(gn, n0 & ~bit);
+            } else {
+                ts.S1.set(gx, ts.S1.get(gx) | (1ull << (k - 64)));
+                ts.S1.set(gn, n1 & ~(1ull << (k - 64)));
+            }
+            ts.Saq.set(gx, (S)(sqx + (S)c.sufq[k])); ts.Saq.set(gn, (S)(sqn - (S)c.sufq[k]));
+            ts.star.set(gx, sx); ts.star.set(gn, sn);
+            ts.Tw.set(gx, tmx); ts.Tw.set(gn, tmn);
+#pragma unroll
+            for (int g = 0; g < MAXT; ++g) tv[g] = (g == gx) ? tmx : ((g == gn) ? tmn : tv[g]);
         }
     }
 
-    // --- path-length cost (Sec. 2.2, Eq. 4)
+    // --- path-length cost (Sec. 2.2, Eq. 4). Shuttle sums in fixed point are exact, so the
+    // order in which fields are visited does not matter: walk the base's BP lists and
+    // route the (at most two) fields that changed BP separately. The plan's shuttle total
+    // is one exact integer; the inspection kernel also keeps it per tour.
+    float kfv[MAXT];
+#pragma unroll
+    for (int g = 0; g < MAXT; ++g) {
+        kfv[g] = 0.f;
+        if ((amask >> g) & 1u) {
+            const M s0 = ts.S0.get(g);
+            const unsigned long long s1 = (SW > 1) ? ts.S1.get(g) : 0ull;
+            const int nsu = popc_m(s0) + (SW > 1 ? popc_m(s1) : 0);
+            kfv[g] = __fdividef((float)nsu, __fmul_rn(__ll2float_rn(cap_sum<SH>(c, s0, s1)), c.cqs));
+        }
+        if (DUMP) ts.Sh.set(g, 0ull);
+    }
+    // rare exact path of Eq. 4: capacity sum of tour g recomputed from its SU set
+    auto ceil_n = [&](int g, float sup, float kf) -> int {
+        const float q = __fmul_rn(sup, kf);
+        const float rq = rintf(q);
+        if (fabsf(q - rq) > q * (1.0f / 2097152.0f)) return (int)ceilf(q);
+        const M s0 = ts.S0.get(g);
+        const unsigned long long s1 = (SW > 1) ? ts.S1.get(g) : 0ull;
+        const int nsu = popc_m(s0) + (SW > 1 ? popc_m(s1) : 0);
+        return exact_ceil(sup, nsu, (double)cap_sum<SH>(c, s0, s1) * c.cqs_d, q);
+    };
+    long long shq = 0;
+    for (int b = 0; b < c.B; ++b) {
+        const int g = x.tour_of_bp(c, b);
+        float kf = kfv[0];
+#pragma unroll
+        for (int t = 1; t < MAXT; ++t)
+            if (g == t) kf = kfv[t];
+        long long acc = 0;
+        const int k0 = c.bp_start[b], k1 = k0 + c.bp_cnt[b];
+        const int bn = 1 + b;
+        for (int kk = k0; kk < k1; ++kk) {
+            const int f = c.field_order[kk];
+            if (x.bp_of_field(c, f) != b) continue;   // moved to another BP: added below
+            const int n = ceil_n(g, c.supply[f], kf);
+            acc += (long long)n * __float2ll_rn(__fmul_rn(c.d(1 + c.B + f, bn), c.dq_inv));
+        }
+        shq += acc;
+        if (DUMP) ts.Sh.set(g, ts.Sh.get(g) + (unsigned long long)acc);
+    }
+    {
+        int mv_f0 = -1, mv_f1 = -1;
+        if (x.kind == 0 && x.sg != x.dg) mv_f0 = x.v;
+        if (x.kind == 2 && c.field_bp[x.v] != c.field_bp[x.w]) { mv_f0 = x.v; mv_f1 = x.w; }
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+            const int f = q == 0 ? mv_f0 : mv_f1;
+            if (f >= 0) {
+                const int b = x.bp_of_field(c, f);
+                const int g = x.tour_of_bp(c, b);
+                float kf = kfv[0];
+#pragma unroll
+                for (int t = 1; t < MAXT; ++t)
+                    if (g == t) kf = kfv[t];
+                const int n = ceil_n(g, c.supply[f], kf);
+                const long long a = (long long)n * __float2ll_rn(__fmul_rn(c.d(1 + c.B + f, 1 + b), c.dq_inv));
+                shq += a;
+                if (DUMP) ts.Sh.set(g, ts.Sh.get(g) + (unsigned long long)a);
+            }
+        }
+    }
     float cost = 0.f;
     for (int g = 0; g < c.T; ++g) {
         if (!((amask >> g) & 1u)) continue;
-        const unsigned long long hm = TM(0, g);
-        unsigned long long sm[2] = {TM(1, g), SW > 1 ? TM(2, g) : 0ull};
-        const int nhu = __popcll(hm);
-        const int nsu = popc_su(sm, SW);
-        long long capq = 0;
-#pragma unroll
-        for (int w = 0; w < SW; ++w) {
-            unsigned long long r = sm[w];
-            while (r) {
-                const int k = __ffsll((long long)r) - 1;
-                r &= r - 1;
-                capq += c.sucq[w * 64 + k];
-            }
-        }
-        const float capf = __fmul_rn(__ll2float_rn(capq), c.cqs);
-        const float kf = __fdiv_rn((float)nsu, capf);
-        const double capd = (double)capq * c.cqs_d;
-        float shuttle = 0.f;
-        const int nb = x.tour_len(c, g);
-        for (int jj = 0; jj < nb; ++jj) {
-            const int b = x.bp_at(c, g, jj);
-            const int nf = x.bp_len(c, b);
-            for (int k = 0; k < nf; ++k) {
-                const int f = x.field_at(c, b, k);
-                const float s = c.supply[f];
-                const float q = __fmul_rn(s, kf);
-                const float rq = rintf(q);
-                int n;
-                if (fabsf(q - rq) <= q * (1.0f / 2097152.0f)) n = exact_ceil(s, nsu, capd, q);
-                else n = (int)ceilf(q);
-                shuttle = __fmaf_rn((float)(2 * n), c.d(1 + c.B + f, 1 + b), shuttle);
-            }
-        }
-        const float tc = __fadd_rn(__fadd_rn(__fmul_rn((float)nhu, TF(F_LHU, g)), __fmul_rn((float)nsu, TF(F_LSU, g))),
-                                   shuttle);
-        cost = __fadd_rn(cost, tc);
+        const M hm = ts.Hm.get(g);
+        const M s0 = ts.S0.get(g);
+        const unsigned long long s1 = (SW > 1) ? ts.S1.get(g) : 0ull;
+        const int nhu = popc_m(hm);
+        const int nsu = popc_m(s0) + (SW > 1 ? popc_m(s1) : 0);
+        const float route = __fadd_rn(__fmul_rn((float)nhu, ts.LHU.get(g)), __fmul_rn((float)nsu, ts.LSU.get(g)));
+        cost = __fadd_rn(cost, route);
         if (DUMP) {
+            const float shuttle = __fmul_rn(__fmul_rn(__ll2float_rn((long long)ts.Sh.get(g)), c.dq_scale), 2.0f);
             if (o_nhu) o_nhu[g] = (int16_t)nhu;
             if (o_nsu) o_nsu[g] = (int16_t)nsu;
-            if (o_tc) o_tc[g] = TF(F_TC, g);
-            if (o_tw) o_tw[g] = TF(F_TW, g);
-            if (o_tcost) o_tcost[g] = tc;
+            if (o_tc) o_tc[g] = ts.Tc.get(g);
+            if (o_tw) o_tw[g] = ts.Tw.get(g);
+            if (o_tcost) o_tcost[g] = __fadd_rn(route, shuttle);
             if (o_hu) {
-                unsigned long long r = hm;
-                while (r) { const int k = __ffsll((long long)r) - 1; r &= r - 1; o_hu[c.hu_id[k]] = (int16_t)g; }
+                M r = hm;
+                while (r) { const int k = ffs_m(r); r &= r - 1; o_hu[c.hu_id[k]] = (int16_t)g; }
             }
             if (o_su) {
-#pragma unroll
-                for (int w = 0; w < SW; ++w) {
-                    unsigned long long r = sm[w];
-                    while (r) { const int k = __ffsll((long long)r) - 1; r &= r - 1; o_su[c.su_id[w * 64 + k]] = (int16_t)g; }
+                M r = s0;
+                while (r) { const int k = ffs_m(r); r &= r - 1; o_su[c.su_id[k]] = (int16_t)g; }
+                if (SW > 1) {
+                    unsigned long long r2 = s1;
+                    while (r2) { const int k = ffs_m(r2); r2 &= r2 - 1; o_su[c.su_id[64 + k]] = (int16_t)g; }
                 }
             }
         }
     }
+    cost = __fadd_rn(cost, __fmul_rn(__fmul_rn(__ll2float_rn(shq), c.dq_scale), 2.0f));
     // --- completion-time gate (Sec. 2.5)
     if ((p.gate == 1 && tmax > tmax_star) || (p.gate == 2 && tmax >= tmax_star)) cost = __int_as_float(0x7f800000);
     out.cost = cost;
     out.tmax = tmax;
     return out;
-#undef TF
-#undef TQ
-#undef TM
 #undef FOR_ACTIVE
 }
 
@@ -544,10 +731,10 @@ __device__ ScoreOut score_candidate(const Ctx &c, const SearchParams &p, const M
 __host__ __device__ inline size_t align16(size_t x) { return (x + 15) & ~size_t(15); }
 
 struct SmemPlan {
-    size_t off_blob, off_plan, off_derived, off_supq, off_bad, off_tf, off_tq, off_tm, off_qidx, off_qmv, total;
+    size_t off_blob, off_plan, off_derived, off_supq, off_bad, off_base_agg, off_tour, off_qidx, off_qmv, total;
 };
 
-__host__ __device__ inline SmemPlan carve(int maxt, int sw, int threads, int max_prefix, int max_plan_len, int max_F,
+__host__ __device__ inline SmemPlan carve(size_t tour_bytes, int threads, int max_prefix, int max_plan_len, int max_F,
                                           int max_B, int max_T)
 {
     SmemPlan s;
@@ -557,27 +744,24 @@ __host__ __device__ inline SmemPlan carve(int maxt, int sw, int threads, int max
     s.off_derived = o; o += align16((size_t)(max_T + 3 * max_B + 2 * max_F) * 2);
     s.off_supq = o; o += align16((size_t)max_B * 8);
     s.off_bad = o; o += align16((size_t)max_B);
-    s.off_tf = o; o += align16((size_t)NFLT * maxt * threads * 4);
-    s.off_tq = o; o += align16((size_t)NI64 * maxt * threads * 8);
-    s.off_tm = o; o += align16((size_t)(1 + sw) * maxt * threads * 8);
-    s.off_qidx = o; o += align16((size_t)QUEUE_PER_THREAD * threads * 4);
-    s.off_qmv = o; o += align16((size_t)QUEUE_PER_THREAD * threads * 8);
+    s.off_base_agg = o; o += align16((size_t)4 * max_T * 4);
+    s.off_tour = o; o += align16(tour_bytes);
+    s.off_qidx = o; o += align16((size_t)(threads / 32) * WQ * 4);
+    s.off_qmv = o; o += align16((size_t)(threads / 32) * WQ * 8);
     s.total = o;
     return s;
 }
 
 template <class SH>
-__host__ __device__ inline SmemPlan carve_shape(int threads, int max_prefix, int max_plan_len, int max_F, int max_B,
-                                                int max_T)
+__host__ __device__ inline SmemPlan carve_shape(int max_prefix, int max_plan_len, int max_F, int max_B, int max_T)
 {
-    return carve(SH::MAXT, SH::SW, threads, max_prefix, max_plan_len, max_F, max_B, max_T);
+    return carve(TourState<SH>::bytes(), SH::NT, max_prefix, max_plan_len, max_F, max_B, max_T);
 }
 
 struct BlockShared {
     uint64_t mbar;
     uint32_t phase;
     int32_t staged;
-    int32_t qcount;
     int32_t nbad;
     int32_t last;
     int32_t use_best;
@@ -586,8 +770,8 @@ struct BlockShared {
     float redt[32];
 };
 
-// Stage instance `inst` (tables by bulk copy, base plan, derived tables).
-// Returns false if the bounded wait gave up (error flag set).
+// Stage instance `inst` (tables by bulk copy, base plan, derived tables, base
+// tour aggregates). Returns false if the bounded wait gave up (error flag set).
 template <class SH>
 __device__ bool stage_instance(const InstMeta &M, BlockShared &bs, unsigned char *smem, const SmemPlan &sp,
                                const SearchParams &p, int use_best_override, uint32_t iter_override, Ctx &c)
@@ -637,7 +821,9 @@ __device__ bool stage_instance(const InstMeta &M, BlockShared &bs, unsigned char
     c.hurq = (const long long *)(blob + M.L.off_hurq);
     c.sufq = (const long long *)(blob + M.L.off_sufq);
     c.sucq = (const long long *)(blob + M.L.off_sucq);
-    c.suspd = (const float *)(blob + M.L.off_suspd);
+    c.suinv = (const float *)(blob + M.L.off_suinv);
+    c.sufill = (const float *)(blob + M.L.off_sufill);
+    c.rcp = (const float *)(blob + M.L.off_rcp);
     c.sugrp = (const int *)(blob + M.L.off_sugrp);
     c.hudeal_m = (const unsigned long long *)(blob + M.L.off_hudeal_m);
     c.hudeal_q = (const long long *)(blob + M.L.off_hudeal_q);
@@ -646,6 +832,7 @@ __device__ bool stage_instance(const InstMeta &M, BlockShared &bs, unsigned char
     c.hu_id = (const int *)(blob + M.L.off_hu_id);
     c.su_id = (const int *)(blob + M.L.off_su_id);
     c.inv_v = M.inv_hu_speed; c.rqs = M.rq_scale; c.fqs = M.fq_scale; c.cqs = M.cq_scale; c.cqs_d = M.cq_scale_d;
+    c.dq_inv = M.dq_inv; c.dq_scale = M.dq_scale;
     const int B = M.B, T = M.T, F = M.F;
     c.bp_order = plan;
     c.tour_cnt = plan + B;
@@ -656,8 +843,10 @@ __device__ bool stage_instance(const InstMeta &M, BlockShared &bs, unsigned char
     int16_t *field_bp = der + T + 3 * B, *field_pos = der + T + 3 * B + F;
     long long *base_supq = (long long *)(smem + sp.off_supq);
     int8_t *bad = (int8_t *)(smem + sp.off_bad);
+    float *agg = (float *)(smem + sp.off_base_agg);
     c.tour_start = tour_start; c.bp_start = bp_start; c.bp_tour = bp_tour; c.bp_pos = bp_pos;
     c.field_bp = field_bp; c.field_pos = field_pos; c.base_supq = base_supq; c.bad = bad;
+    c.bLHU = agg; c.bLSU = agg + T; c.bA = agg + 2 * T; c.bDB2 = agg + 3 * T;
     if (tid == 0) {
         int s = 0;
         for (int g = 0; g < T; ++g) { tour_start[g] = (int16_t)s; s += c.tour_cnt[g]; }
@@ -685,6 +874,16 @@ __device__ bool stage_instance(const InstMeta &M, BlockShared &bs, unsigned char
         int nb = 0;
         for (int b = 0; b < B; ++b) nb += bad[b];
         bs.nbad = nb;
+    }
+    // base plan's tour aggregates, traced with the same code as candidates
+    for (int g = tid; g < T; g += nt) {
+        View x;
+        x.kind = 4; x.v = x.w = x.sg = x.sp = x.dg = x.dp = -1;
+        const int nb = c.tour_cnt[g];
+        TourAgg t;
+        t.LHU = t.LSU = t.A = t.DB2 = 0.f;
+        if (nb > 0) t = trace_tour(c, x, g, nb);
+        agg[g] = t.LHU; agg[T + g] = t.LSU; agg[2 * T + g] = t.A; agg[3 * T + g] = t.DB2;
     }
     __syncthreads();
     c.nbad = bs.nbad;
@@ -719,30 +918,28 @@ __device__ void write_plan(const Ctx &c, const MoveRec &m, int16_t *out)
 // The search iteration kernel
 // ---------------------------------------------------------------------------
 template <class SH>
-__global__ void __launch_bounds__(SH::NT) search_iteration_kernel(const InstMeta *__restrict__ meta,
-                                                               const WorkItem *__restrict__ work, int32_t n_work,
-                                                               SearchParams prm, SmemPlan sp,
-                                                               unsigned long long *__restrict__ slot_key,
-                                                               float *__restrict__ slot_tmax,
-                                                               const int32_t *__restrict__ slot_base)
+__global__ void __launch_bounds__(SH::NT, SH::MINB) search_iteration_kernel(const InstMeta *__restrict__ meta,
+                                                                  const WorkItem *__restrict__ work, int32_t n_work,
+                                                                  SearchParams prm, SmemPlan sp,
+                                                                  unsigned long long *__restrict__ slot_key,
+                                                                  float *__restrict__ slot_tmax,
+                                                                  const int32_t *__restrict__ slot_base)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ BlockShared bs;
-    const int tid = threadIdx.x, nt = blockDim.x;
+    const int tid = threadIdx.x;
+    const int lane = tid & 31, warp = tid >> 5;
+    constexpr int NT = SH::NT;
     if (tid == 0) {
         mbar_init(&bs.mbar, 1);
         fence_mbar_init();
         bs.phase = 0;
         bs.staged = -1;
-        bs.qcount = 0;
     }
     __syncthreads();
-    float *tf = (float *)(smem + sp.off_tf);
-    long long *tq = (long long *)(smem + sp.off_tq);
-    unsigned long long *tm = (unsigned long long *)(smem + sp.off_tm);
-    int32_t *qidx = (int32_t *)(smem + sp.off_qidx);
-    int16_t *qmv = (int16_t *)(smem + sp.off_qmv);
-    const int QN = QUEUE_PER_THREAD * nt;
+    unsigned char *tstate = smem + sp.off_tour;
+    int32_t *qidx = (int32_t *)(smem + sp.off_qidx) + warp * WQ;
+    int2 *qmv = (int2 *)(smem + sp.off_qmv) + warp * WQ;
     Ctx c;
     for (int w = blockIdx.x; w < n_work; w += gridDim.x) {
         const WorkItem wi = work[w];
@@ -750,6 +947,7 @@ __global__ void __launch_bounds__(SH::NT) search_iteration_kernel(const InstMeta
         if (bs.staged != wi.inst) {
             if (!stage_instance<SH>(M, bs, smem, sp, prm, -1, 0xffffffffu, c)) return;
             if (tid == 0) bs.staged = wi.inst;
+            __syncthreads();
         }
         const float tmax_star = M.state->tmaxstar;
         const uint32_t iter = bs.iter;
@@ -757,10 +955,11 @@ __global__ void __launch_bounds__(SH::NT) search_iteration_kernel(const InstMeta
         const int c1 = min(c0 + M.tile, M.n_cand);
         unsigned long long best = ~0ull;
         float best_t = 0.f;
-        for (int q0 = c0; q0 < c1; q0 += QN) {
-            // phase A: draw moves, exact demand check, compact the feasible ones
-            for (int qq = 0; qq < QN; qq += nt) {
-                const int i = q0 + qq + tid;
+        // each warp: draw 32 moves at a time, queue the feasible ones, score 32 queued at a time
+        int qhead = 0, qcount = 0;   // warp-uniform ring-buffer state
+        for (int base = c0 + warp * 32; base < c1 || qcount > 0; base += NT) {
+            if (base < c1) {
+                const int i = base + lane;
                 bool feas = false;
                 MoveRec m = {4, 0, 0, 0};
                 if (i < c1) {
@@ -772,30 +971,31 @@ __global__ void __launch_bounds__(SH::NT) search_iteration_kernel(const InstMeta
                     }
                 }
                 const unsigned ball = __ballot_sync(0xffffffffu, feas);
-                int base = 0;
-                if ((tid & 31) == 0 && ball) base = atomicAdd(&bs.qcount, __popc(ball));
-                base = __shfl_sync(0xffffffffu, base, 0);
                 if (feas) {
-                    const int pos = base + __popc(ball & ((1u << (tid & 31)) - 1u));
-                    qidx[pos] = i;
-                    qmv[pos * 4 + 0] = (int16_t)m.kind; qmv[pos * 4 + 1] = (int16_t)m.v;
-                    qmv[pos * 4 + 2] = (int16_t)m.a; qmv[pos * 4 + 3] = (int16_t)m.b;
+                    const int slot = (qhead + qcount + __popc(ball & ((1u << lane) - 1u))) & (WQ - 1);
+                    qidx[slot] = i;
+                    qmv[slot] = make_int2((m.kind & 0xffff) | (m.v << 16), (m.a & 0xffff) | (m.b << 16));
                 }
+                qcount += __popc(ball);
+                __syncwarp();
             }
-            __syncthreads();
-            const int nq = bs.qcount;
-            // phase B: score the queued candidates, one per thread
-            for (int q = tid; q < nq; q += nt) {
-                const int i = qidx[q];
-                MoveRec m = {qmv[q * 4], qmv[q * 4 + 1], qmv[q * 4 + 2], qmv[q * 4 + 3]};
-                ScoreOut r = score_candidate<SH, false>(c, prm, m, tmax_star, tf, tq, tm, nt, tid, nullptr, nullptr,
-                                                        nullptr, nullptr, nullptr, nullptr, nullptr);
-                const unsigned long long k = make_key(r.cost, (uint32_t)i);
-                if (k < best) { best = k; best_t = r.tmax; }
+            // score a full warp of queued candidates, or the remainder once the draws are done
+            const int take = (qcount >= 32) ? 32 : ((base + NT >= c1) ? qcount : 0);
+            if (take > 0) {
+                if (lane < take) {
+                    const int slot = (qhead + lane) & (WQ - 1);
+                    const int i = qidx[slot];
+                    const int2 pm = qmv[slot];
+                    const MoveRec m = {pm.x & 0xffff, pm.x >> 16, pm.y & 0xffff, pm.y >> 16};
+                    const ScoreOut r = score_candidate<SH, false>(c, prm, m, tmax_star, tstate, tid, nullptr, nullptr,
+                                                                  nullptr, nullptr, nullptr, nullptr, nullptr);
+                    const unsigned long long k = make_key(r.cost, (uint32_t)i);
+                    if (k < best) { best = k; best_t = r.tmax; }
+                }
+                __syncwarp();
+                qhead = (qhead + take) & (WQ - 1);
+                qcount -= take;
             }
-            __syncthreads();
-            if (tid == 0) bs.qcount = 0;
-            __syncthreads();
         }
         // block argmin: warp shuffle, then across warps
         for (int o = 16; o > 0; o >>= 1) {
@@ -803,10 +1003,10 @@ __global__ void __launch_bounds__(SH::NT) search_iteration_kernel(const InstMeta
             const float ot = __shfl_xor_sync(0xffffffffu, best_t, o);
             if (ok < best) { best = ok; best_t = ot; }
         }
-        if ((tid & 31) == 0) { bs.red[tid >> 5] = best; bs.redt[tid >> 5] = best_t; }
+        if (lane == 0) { bs.red[warp] = best; bs.redt[warp] = best_t; }
         __syncthreads();
         if (tid < 32) {
-            const int nw = nt >> 5;
+            const int nw = NT >> 5;
             best = (tid < nw) ? bs.red[tid] : ~0ull;
             best_t = (tid < nw) ? bs.redt[tid] : 0.f;
             for (int o = 16; o > 0; o >>= 1) {
@@ -879,11 +1079,11 @@ __global__ void __launch_bounds__(SH::NT) search_iteration_kernel(const InstMeta
 // ---------------------------------------------------------------------------
 template <class SH>
 __global__ void __launch_bounds__(SH::NT) score_dump_kernel(const InstMeta *__restrict__ meta, int32_t inst,
-                                                         int32_t use_best, uint32_t iter, float tmax_star, int32_t i0,
-                                                         int32_t n, int32_t identity, SearchParams prm, SmemPlan sp,
-                                                         float *cost, float *tmax, int16_t *moves, int16_t *nhu,
-                                                         int16_t *nsu, float *tcompl, float *twait, float *tcost,
-                                                         int16_t *hu_tour, int16_t *su_tour)
+                                                            int32_t use_best, uint32_t iter, float tmax_star,
+                                                            int32_t i0, int32_t n, int32_t identity, SearchParams prm,
+                                                            SmemPlan sp, float *cost, float *tmax, int16_t *moves,
+                                                            int16_t *nhu, int16_t *nsu, float *tcompl, float *twait,
+                                                            float *tcost, int16_t *hu_tour, int16_t *su_tour)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ BlockShared bs;
@@ -897,14 +1097,15 @@ __global__ void __launch_bounds__(SH::NT) score_dump_kernel(const InstMeta *__re
     const InstMeta &M = meta[inst];
     Ctx c;
     if (!stage_instance<SH>(M, bs, smem, sp, prm, use_best, iter, c)) return;
-    float *tf = (float *)(smem + sp.off_tf);
-    long long *tq = (long long *)(smem + sp.off_tq);
-    unsigned long long *tm = (unsigned long long *)(smem + sp.off_tm);
+    unsigned char *tstate = smem + sp.off_tour;
     const int T = M.T;
     for (int k = blockIdx.x * nt + tid; k < n; k += gridDim.x * nt) {
         const int i = i0 + k;
         MoveRec m = identity ? MoveRec{4, 0, 0, 0} : draw_move(c, prm, (uint32_t)i, iter, M.inst_idx);
-        if (moves) { moves[k * 4] = (int16_t)m.kind; moves[k * 4 + 1] = (int16_t)m.v; moves[k * 4 + 2] = (int16_t)m.a; moves[k * 4 + 3] = (int16_t)m.b; }
+        if (moves) {
+            moves[k * 4] = (int16_t)m.kind; moves[k * 4 + 1] = (int16_t)m.v;
+            moves[k * 4 + 2] = (int16_t)m.a; moves[k * 4 + 3] = (int16_t)m.b;
+        }
         int16_t *o_nhu = nhu ? nhu + (size_t)k * T : nullptr;
         int16_t *o_nsu = nsu ? nsu + (size_t)k * T : nullptr;
         float *o_tc = tcompl ? tcompl + (size_t)k * T : nullptr;
@@ -923,8 +1124,8 @@ __global__ void __launch_bounds__(SH::NT) score_dump_kernel(const InstMeta *__re
         if (o_su) for (int s = 0; s < M.S; ++s) o_su[s] = -1;
         ScoreOut r;
         if (demand_ok(c, m))
-            r = score_candidate<SH, true>(c, prm, m, tmax_star, tf, tq, tm, nt, tid, o_nhu, o_nsu, o_tc, o_tw, o_tk,
-                                          o_hu, o_su);
+            r = score_candidate<SH, true>(c, prm, m, tmax_star, tstate, tid, o_nhu, o_nsu, o_tc, o_tw, o_tk, o_hu,
+                                          o_su);
         else { r.cost = __int_as_float(0x7f800000); r.tmax = __int_as_float(0x7f800000); }
         if (cost) cost[k] = r.cost;
         if (tmax) tmax[k] = r.tmax;
@@ -932,9 +1133,9 @@ __global__ void __launch_bounds__(SH::NT) score_dump_kernel(const InstMeta *__re
 }
 
 template <class SH>
-__global__ void __launch_bounds__(SH::NT) decode_kernel(const InstMeta *__restrict__ meta, int32_t inst, int32_t use_best,
-                                                     uint32_t iter, const int32_t *idx, int32_t n, SearchParams prm,
-                                                     SmemPlan sp, int16_t *plans)
+__global__ void __launch_bounds__(SH::NT) decode_kernel(const InstMeta *__restrict__ meta, int32_t inst,
+                                                        int32_t use_best, uint32_t iter, const int32_t *idx, int32_t n,
+                                                        SearchParams prm, SmemPlan sp, int16_t *plans)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ BlockShared bs;
@@ -963,18 +1164,18 @@ int threads_of(int32_t shape)
 {
     return shape == SHAPE_T4_S64_DSMEM ? ShapeA::NT : shape == SHAPE_T8_S64_DSMEM ? ShapeB::NT : ShapeC::NT;
 }
-int max_su_of(int32_t shape) { return shape == SHAPE_T16_S128_GMEM ? 128 : 64; }
+int max_su_of(int32_t shape) { return shape == SHAPE_T16_S128_GMEM ? 128 : (shape == SHAPE_T4_S64_DSMEM ? 32 : 64); }
 bool dist_in_smem(int32_t shape) { return shape != SHAPE_T16_S128_GMEM; }
 
 static SmemPlan plan_for(const LaunchCfg &cfg)
 {
     switch (cfg.shape) {
     case SHAPE_T4_S64_DSMEM:
-        return carve_shape<ShapeA>(cfg.threads, cfg.max_prefix, cfg.max_plan_len, cfg.max_F, cfg.max_B, cfg.max_T);
+        return carve_shape<ShapeA>(cfg.max_prefix, cfg.max_plan_len, cfg.max_F, cfg.max_B, cfg.max_T);
     case SHAPE_T8_S64_DSMEM:
-        return carve_shape<ShapeB>(cfg.threads, cfg.max_prefix, cfg.max_plan_len, cfg.max_F, cfg.max_B, cfg.max_T);
+        return carve_shape<ShapeB>(cfg.max_prefix, cfg.max_plan_len, cfg.max_F, cfg.max_B, cfg.max_T);
     default:
-        return carve_shape<ShapeC>(cfg.threads, cfg.max_prefix, cfg.max_plan_len, cfg.max_F, cfg.max_B, cfg.max_T);
+        return carve_shape<ShapeC>(cfg.max_prefix, cfg.max_plan_len, cfg.max_F, cfg.max_B, cfg.max_T);
     }
 }
 
@@ -990,7 +1191,8 @@ size_t shared_bytes(int32_t shape, int32_t threads, int32_t max_prefix, int32_t 
 template <class SH>
 static cudaError_t set_attrs(size_t smem)
 {
-    cudaError_t e = cudaFuncSetAttribute(search_iteration_kernel<SH>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e =
+        cudaFuncSetAttribute(search_iteration_kernel<SH>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     e = cudaFuncSetAttribute(score_dump_kernel<SH>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
@@ -1007,22 +1209,22 @@ cudaError_t configure_kernels(int32_t shape, size_t smem)
 }
 
 cudaError_t launch_search_iteration(const LaunchCfg &cfg, const InstMeta *d_meta, const WorkItem *d_work,
-                                          int32_t n_work, SearchParams prm, unsigned long long *slot_key,
-                                          float *slot_tmax, const int32_t *slot_base, cudaStream_t s)
+                                    int32_t n_work, SearchParams prm, unsigned long long *slot_key, float *slot_tmax,
+                                    const int32_t *slot_base, cudaStream_t s)
 {
     const SmemPlan sp = plan_for(cfg);
     switch (cfg.shape) {
     case SHAPE_T4_S64_DSMEM:
-        search_iteration_kernel<ShapeA><<<cfg.grid, cfg.threads, sp.total, s>>>(d_meta, d_work, n_work, prm, sp,
-                                                                              slot_key, slot_tmax, slot_base);
+        search_iteration_kernel<ShapeA><<<cfg.grid, ShapeA::NT, sp.total, s>>>(d_meta, d_work, n_work, prm, sp,
+                                                                                slot_key, slot_tmax, slot_base);
         break;
     case SHAPE_T8_S64_DSMEM:
-        search_iteration_kernel<ShapeB><<<cfg.grid, cfg.threads, sp.total, s>>>(d_meta, d_work, n_work, prm, sp,
-                                                                              slot_key, slot_tmax, slot_base);
+        search_iteration_kernel<ShapeB><<<cfg.grid, ShapeB::NT, sp.total, s>>>(d_meta, d_work, n_work, prm, sp,
+                                                                                slot_key, slot_tmax, slot_base);
         break;
     default:
-        search_iteration_kernel<ShapeC><<<cfg.grid, cfg.threads, sp.total, s>>>(d_meta, d_work, n_work, prm, sp,
-                                                                              slot_key, slot_tmax, slot_base);
+        search_iteration_kernel<ShapeC><<<cfg.grid, ShapeC::NT, sp.total, s>>>(d_meta, d_work, n_work, prm, sp,
+                                                                                slot_key, slot_tmax, slot_base);
     }
     return cudaGetLastError();
 }
@@ -1034,15 +1236,16 @@ cudaError_t launch_score_dump(const LaunchCfg &cfg, const InstMeta *d_meta, int3
                               int16_t *d_su_tour, cudaStream_t s)
 {
     const SmemPlan sp = plan_for(cfg);
-    int grid = (n + cfg.threads - 1) / cfg.threads;
+    const int nt = threads_of(cfg.shape);
+    int grid = (n + nt - 1) / nt;
     if (grid > cfg.grid) grid = cfg.grid;
     if (grid < 1) grid = 1;
 #define DUMP_ARGS d_meta, inst, use_best, iter, tmax_star, i0, n, identity, prm, sp, d_cost, d_tmax, d_moves, d_nhu, \
                   d_nsu, d_tcompl, d_twait, d_tcost, d_hu_tour, d_su_tour
     switch (cfg.shape) {
-    case SHAPE_T4_S64_DSMEM: score_dump_kernel<ShapeA><<<grid, cfg.threads, sp.total, s>>>(DUMP_ARGS); break;
-    case SHAPE_T8_S64_DSMEM: score_dump_kernel<ShapeB><<<grid, cfg.threads, sp.total, s>>>(DUMP_ARGS); break;
-    default: score_dump_kernel<ShapeC><<<grid, cfg.threads, sp.total, s>>>(DUMP_ARGS);
+    case SHAPE_T4_S64_DSMEM: score_dump_kernel<ShapeA><<<grid, nt, sp.total, s>>>(DUMP_ARGS); break;
+    case SHAPE_T8_S64_DSMEM: score_dump_kernel<ShapeB><<<grid, nt, sp.total, s>>>(DUMP_ARGS); break;
+    default: score_dump_kernel<ShapeC><<<grid, nt, sp.total, s>>>(DUMP_ARGS);
     }
 #undef DUMP_ARGS
     return cudaGetLastError();
@@ -1053,18 +1256,19 @@ cudaError_t launch_decode(const LaunchCfg &cfg, const InstMeta *d_meta, int32_t 
                           cudaStream_t s)
 {
     const SmemPlan sp = plan_for(cfg);
-    int grid = (n + cfg.threads - 1) / cfg.threads;
+    const int nt = threads_of(cfg.shape);
+    int grid = (n + nt - 1) / nt;
     if (grid > cfg.grid) grid = cfg.grid;
     if (grid < 1) grid = 1;
     switch (cfg.shape) {
     case SHAPE_T4_S64_DSMEM:
-        decode_kernel<ShapeA><<<grid, cfg.threads, sp.total, s>>>(d_meta, inst, use_best, iter, d_idx, n, prm, sp, d_plans);
+        decode_kernel<ShapeA><<<grid, nt, sp.total, s>>>(d_meta, inst, use_best, iter, d_idx, n, prm, sp, d_plans);
         break;
     case SHAPE_T8_S64_DSMEM:
-        decode_kernel<ShapeB><<<grid, cfg.threads, sp.total, s>>>(d_meta, inst, use_best, iter, d_idx, n, prm, sp, d_plans);
+        decode_kernel<ShapeB><<<grid, nt, sp.total, s>>>(d_meta, inst, use_best, iter, d_idx, n, prm, sp, d_plans);
         break;
     default:
-        decode_kernel<ShapeC><<<grid, cfg.threads, sp.total, s>>>(d_meta, inst, use_best, iter, d_idx, n, prm, sp, d_plans);
+        decode_kernel<ShapeC><<<grid, nt, sp.total, s>>>(d_meta, inst, use_best, iter, d_idx, n, prm, sp, d_plans);
     }
     return cudaGetLastError();
 }
