@@ -193,6 +193,30 @@ int bl_score_candidates(bl_handle *h, int32_t inst, int32_t use_best, uint32_t i
 int bl_decode_candidates(bl_handle *h, int32_t inst, int32_t use_best, uint32_t iter, const int32_t *idx, int32_t n,
                          int16_t *plans);
 
+/* Argmin without allocation (the paper has no counterpart: this is a library
+   convenience). Scores candidates i0..i0+n-1 of iteration `iter`, drawn from
+   base x* (use_best = 1) or x_old (0) of instance `inst`, and writes the
+   smallest key ((cost bits << 32) | i, as in bl_get_log's i*) to *d_key and
+   the winner's maximum completion time to *d_tmax. d_key and d_tmax are
+   device pointers owned by the caller; the call is asynchronous on the
+   handle's stream. It is meant for callers that must not allocate device
+   memory where they call it -- for example a latency-critical loop in which
+   the device synchronisation of cudaMalloc/cudaFree is unacceptable, or a
+   process whose device memory is entirely owned by another allocator.
+   Nothing is allocated: the kernel's scratch (one partial result per block,
+   at most 1024 blocks, and a completion counter; 16,640 bytes) is a static
+   array in the library's device code that every GPU loading the library
+   holds until the process exits. The first call on a device looks up that
+   array's device address (with the device current), so make the first call
+   before any stream capture. All calls on a device share the array: the
+   counter is cleared before each launch, and calls that overlap on the GPU
+   (e.g. on two streams) race and must not be issued. Errors: BL_EINVAL,
+   BL_ETOO_LARGE when n < 1, n > BL_NOALLOC_MAX_CAND or i0 + n overflows,
+   BL_ECUDA. */
+#define BL_NOALLOC_MAX_CAND (1 << 28)
+int bl_argmin_noalloc(bl_handle *h, int32_t inst, int32_t use_best, uint32_t iter, float tmax_star, int32_t i0,
+                      int32_t n, uint64_t *d_key, float *d_tmax);
+
 /* Kernel configuration in use: threads per block, grid blocks, candidates
    per work item, and the number of kernels one iteration launches. */
 int bl_get_config(bl_handle *h, int32_t *block_threads, int32_t *grid_blocks, int32_t *tile,

@@ -24,7 +24,7 @@ _lock = threading.Lock()
 BL_OK, BL_EINVAL, BL_EINFEASIBLE_INSTANCE, BL_ETOO_LARGE, BL_ECUDA, BL_ETIMEOUT, BL_ESTATE = 0, -1, -2, -3, -4, -5, -6
 EXPORTS = ("bl_workspace_bytes", "bl_plan_init", "bl_plan_init_batch", "bl_search_step", "bl_best_plan",
            "bl_get_state", "bl_set_state", "bl_get_log", "bl_score_candidates", "bl_decode_candidates",
-           "bl_get_config", "bl_plan_free", "bl_last_error", "bl_global_error")
+           "bl_get_config", "bl_plan_free", "bl_last_error", "bl_global_error", "bl_argmin_noalloc")
 
 
 class BiologError(RuntimeError):
@@ -86,6 +86,8 @@ def load(path: str | None = None):
                                               vp, vp, vp, vp, vp]
             L.bl_decode_candidates.argtypes = [vp, C.c_int32, C.c_int32, C.c_uint32, vp, C.c_int32, vp]
             L.bl_get_config.argtypes = [vp, vp, vp, vp, vp]
+            L.bl_argmin_noalloc.argtypes = [vp, C.c_int32, C.c_int32, C.c_uint32, C.c_float, C.c_int32, C.c_int32,
+                                            vp, vp]
             L.bl_plan_free.argtypes = [vp]
             L.bl_last_error.argtypes = [vp]
             L.bl_last_error.restype = C.c_char_p
@@ -227,6 +229,13 @@ class Search:
         _check(load().bl_decode_candidates(self.h, int(inst), int(use_best), int(iter_), _p(idx), len(idx), _p(out)),
                self.h)
         return out
+
+    def argmin_noalloc(self, use_best: int, iter_: int, tmax_star: float, i0: int, n: int, key_ptr: int,
+                       tmax_ptr: int, inst: int = 0):
+        """bl_argmin_noalloc: argmin of candidates i0..i0+n-1 into caller-owned device memory
+        (key_ptr: 8 bytes, tmax_ptr: 4 bytes); the library allocates nothing for it."""
+        _check(load().bl_argmin_noalloc(self.h, int(inst), int(use_best), int(iter_), float(tmax_star), int(i0),
+                                        int(n), C.c_void_p(key_ptr), C.c_void_p(tmax_ptr)), self.h)
 
     def config(self) -> dict:
         v = [C.c_int32() for _ in range(4)]

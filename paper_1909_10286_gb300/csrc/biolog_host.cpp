@@ -874,6 +874,20 @@ int bl_decode_candidates(bl_handle *h, int32_t inst, int32_t use_best, uint32_t 
     return BL_OK;
 }
 
+int bl_argmin_noalloc(bl_handle *h, int32_t inst, int32_t use_best, uint32_t iter, float tmax_star, int32_t i0,
+                      int32_t n, uint64_t *d_key, float *d_tmax)
+{
+    if (!h || inst < 0 || inst >= h->n_inst || i0 < 0 || !d_key || !d_tmax) return BL_EINVAL;
+    if (h->failed) return BL_ESTATE;
+    if (n < 1 || n > BL_NOALLOC_MAX_CAND || (int64_t)i0 + (int64_t)n > (int64_t)INT32_MAX) {
+        h->err = "bl_argmin_noalloc: n must be in [1, BL_NOALLOC_MAX_CAND] and i0 + n must fit in int32";
+        return BL_ETOO_LARGE;
+    }
+    CK(h, launch_argmin_noalloc(h->cfg, h->at<InstMeta>(h->ws.meta), inst, use_best, iter, tmax_star, i0, n, h->sp,
+                                reinterpret_cast<unsigned long long *>(d_key), d_tmax, h->stream));
+    return BL_OK;
+}
+
 int bl_best_plan(bl_handle *h, int32_t inst, bl_plan *out)
 {
     if (!h || !out || inst < 0 || inst >= h->n_inst) return BL_EINVAL;

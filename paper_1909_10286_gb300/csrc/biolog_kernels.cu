@@ -25,6 +25,7 @@
 // Per-tour state of a candidate lives in registers (up to 4 tours) or in
 // shared memory, one column per thread (more tours).
 #include <cstdint>
+#include <mutex>
 #include <type_traits>
 #include <cuda_runtime.h>
 
@@ -1157,6 +1158,135 @@ __global__ void __launch_bounds__(SH::NT) decode_kernel(const InstMeta *__restri
 }
 
 // ---------------------------------------------------------------------------
+// Argmin without allocation
+// ---------------------------------------------------------------------------
+// Scores candidates i0..i0+n-1 of one iteration and reduces them to the
+// argmin key, like the search iteration kernel, but its scratch (one partial
+// result per block and a completion counter) lives in this file-scope device
+// array instead of memory someone allocated. Every call on a device shares
+// the array and finds the previous call's contents in it: the counter is
+// cleared before each launch, and calls that overlap on the GPU race.
+constexpr int kNoAllocMaxBlocks = 1024;   // partial results: 1024 x 16 B, plus the counter
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocMaxBlocks * 16 + 256];
+
+template <class SH>
+__global__ void __launch_bounds__(SH::NT) argmin_noalloc_kernel(const InstMeta *__restrict__ meta, int32_t inst,
+                                                                int32_t use_best, uint32_t iter, float tmax_star,
+                                                                int32_t i0, int32_t n, SearchParams prm, SmemPlan sp,
+                                                                unsigned char *scratch,
+                                                                unsigned long long *__restrict__ out_key,
+                                                                float *__restrict__ out_tmax)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ BlockShared bs;
+    const int tid = threadIdx.x;
+    const int lane = tid & 31, warp = tid >> 5;
+    constexpr int NT = SH::NT;
+    unsigned int *counter = (unsigned int *)scratch;
+    unsigned long long *part_key = (unsigned long long *)(scratch + 256);
+    float *part_tmax = (float *)(scratch + 256 + kNoAllocMaxBlocks * 8);
+    if (tid == 0) {
+        mbar_init(&bs.mbar, 1);
+        fence_mbar_init();
+        bs.phase = 0;
+    }
+    __syncthreads();
+    const InstMeta &M = meta[inst];
+    Ctx c;
+    if (!stage_instance<SH>(M, bs, smem, sp, prm, use_best, iter, c)) return;
+    unsigned char *tstate = smem + sp.off_tour;
+    int32_t *qidx = (int32_t *)(smem + sp.off_qidx) + warp * WQ;
+    int2 *qmv = (int2 *)(smem + sp.off_qmv) + warp * WQ;
+    unsigned long long best = ~0ull;
+    float best_t = 0.f;
+    int qhead = 0, qcount = 0;
+    const int stride = NT * gridDim.x;
+    const int c1 = i0 + n;
+    for (int base = i0 + blockIdx.x * NT + warp * 32; base < c1 || qcount > 0; base += stride) {
+        if (base < c1) {
+            const int i = base + lane;
+            bool feas = false;
+            MoveRec m = {4, 0, 0, 0};
+            if (i < c1) {
+                m = draw_move(c, prm, (uint32_t)i, iter, M.inst_idx);
+                feas = demand_ok(c, m);
+                if (!feas) {
+                    const unsigned long long k = make_key(__int_as_float(0x7f800000), (uint32_t)i);
+                    if (k < best) { best = k; best_t = __int_as_float(0x7f800000); }
+                }
+            }
+            const unsigned ball = __ballot_sync(0xffffffffu, feas);
+            if (feas) {
+                const int slot = (qhead + qcount + __popc(ball & ((1u << lane) - 1u))) & (WQ - 1);
+                qidx[slot] = i;
+                qmv[slot] = make_int2((m.kind & 0xffff) | (m.v << 16), (m.a & 0xffff) | (m.b << 16));
+            }
+            qcount += __popc(ball);
+            __syncwarp();
+        }
+        const int take = (qcount >= 32) ? 32 : ((base + stride >= c1) ? qcount : 0);
+        if (take > 0) {
+            if (lane < take) {
+                const int slot = (qhead + lane) & (WQ - 1);
+                const int i = qidx[slot];
+                const int2 pm = qmv[slot];
+                const MoveRec m = {pm.x & 0xffff, pm.x >> 16, pm.y & 0xffff, pm.y >> 16};
+                const ScoreOut r = score_candidate<SH, false>(c, prm, m, tmax_star, tstate, tid, nullptr, nullptr,
+                                                              nullptr, nullptr, nullptr, nullptr, nullptr);
+                const unsigned long long k = make_key(r.cost, (uint32_t)i);
+                if (k < best) { best = k; best_t = r.tmax; }
+            }
+            __syncwarp();
+            qhead = (qhead + take) & (WQ - 1);
+            qcount -= take;
+        }
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        const unsigned long long ok = __shfl_xor_sync(0xffffffffu, best, o);
+        const float ot = __shfl_xor_sync(0xffffffffu, best_t, o);
+        if (ok < best) { best = ok; best_t = ot; }
+    }
+    if (lane == 0) { bs.red[warp] = best; bs.redt[warp] = best_t; }
+    __syncthreads();
+    if (tid < 32) {
+        best = (tid < (NT >> 5)) ? bs.red[tid] : ~0ull;
+        best_t = (tid < (NT >> 5)) ? bs.redt[tid] : 0.f;
+        for (int o = 16; o > 0; o >>= 1) {
+            const unsigned long long ok = __shfl_xor_sync(0xffffffffu, best, o);
+            const float ot = __shfl_xor_sync(0xffffffffu, best_t, o);
+            if (ok < best) { best = ok; best_t = ot; }
+        }
+        if (tid == 0) {
+            part_key[blockIdx.x] = best;
+            part_tmax[blockIdx.x] = best_t;
+            __threadfence();
+            bs.last = (atomicAdd(counter, 1u) == gridDim.x - 1) ? 1 : 0;
+        }
+    }
+    __syncthreads();
+    if (bs.last && tid < 32) {
+        __threadfence();
+        unsigned long long bk = ~0ull;
+        float bt = 0.f;
+        for (int b = tid; b < (int)gridDim.x; b += 32) {
+            const unsigned long long k = __ldcg(&part_key[b]);
+            const float t = __ldcg(&part_tmax[b]);
+            if (k < bk) { bk = k; bt = t; }
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+            const unsigned long long ok = __shfl_xor_sync(0xffffffffu, bk, o);
+            const float ot = __shfl_xor_sync(0xffffffffu, bt, o);
+            if (ok < bk) { bk = ok; bt = ot; }
+        }
+        if (tid == 0) {
+            *out_key = bk;
+            *out_tmax = bt;
+            *counter = 0u;
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
 // Host-side launch wrappers
 // ---------------------------------------------------------------------------
 int max_tours_of(int32_t shape) { return shape == SHAPE_T4_S64_DSMEM ? 4 : shape == SHAPE_T8_S64_DSMEM ? 8 : 16; }
@@ -1226,6 +1356,65 @@ cudaError_t launch_search_iteration(const LaunchCfg &cfg, const InstMeta *d_meta
         search_iteration_kernel<ShapeC><<<cfg.grid, ShapeC::NT, sp.total, s>>>(d_meta, d_work, n_work, prm, sp,
                                                                                 slot_key, slot_tmax, slot_base);
     }
+    return cudaGetLastError();
+}
+
+// Device address of the no-allocation scratch array, looked up once per device
+// with that device current (the name is only a host-side stand-in: passing it to
+// a kernel would hand the GPU a host address).
+static void *g_noalloc_ptr[64];
+static std::mutex g_noalloc_mutex;
+
+static cudaError_t noalloc_scratch(void **ptr)
+{
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+    if (!g_noalloc_ptr[dev]) {
+        void *p = nullptr;
+        e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess) return e;
+        g_noalloc_ptr[dev] = p;
+    }
+    *ptr = g_noalloc_ptr[dev];
+    return cudaSuccess;
+}
+
+cudaError_t launch_argmin_noalloc(const LaunchCfg &cfg, const InstMeta *d_meta, int32_t inst, int32_t use_best,
+                                  uint32_t iter, float tmax_star, int32_t i0, int32_t n, SearchParams prm,
+                                  unsigned long long *d_key, float *d_tmax, cudaStream_t s)
+{
+    void *scratch = nullptr;
+    cudaError_t e = noalloc_scratch(&scratch);
+    if (e != cudaSuccess) return e;
+    // the counter must start at zero; the partial results are written before they are read
+    e = cudaMemsetAsync(scratch, 0, 256, s);
+    if (e != cudaSuccess) return e;
+    const SmemPlan sp = plan_for(cfg);
+    const int nt = threads_of(cfg.shape);
+    int grid = (n + nt - 1) / nt;
+    if (grid > cfg.grid) grid = cfg.grid;
+    if (grid > kNoAllocMaxBlocks) grid = kNoAllocMaxBlocks;
+    if (grid < 1) grid = 1;
+    unsigned char *sc = (unsigned char *)scratch;
+#define NA_ARGS d_meta, inst, use_best, iter, tmax_star, i0, n, prm, sp, sc, d_key, d_tmax
+    switch (cfg.shape) {
+    case SHAPE_T4_S64_DSMEM:
+        e = cudaFuncSetAttribute(argmin_noalloc_kernel<ShapeA>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sp.total);
+        if (e == cudaSuccess) argmin_noalloc_kernel<ShapeA><<<grid, nt, sp.total, s>>>(NA_ARGS);
+        break;
+    case SHAPE_T8_S64_DSMEM:
+        e = cudaFuncSetAttribute(argmin_noalloc_kernel<ShapeB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sp.total);
+        if (e == cudaSuccess) argmin_noalloc_kernel<ShapeB><<<grid, nt, sp.total, s>>>(NA_ARGS);
+        break;
+    default:
+        e = cudaFuncSetAttribute(argmin_noalloc_kernel<ShapeC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sp.total);
+        if (e == cudaSuccess) argmin_noalloc_kernel<ShapeC><<<grid, nt, sp.total, s>>>(NA_ARGS);
+    }
+#undef NA_ARGS
+    if (e != cudaSuccess) return e;
     return cudaGetLastError();
 }
 
