@@ -60,7 +60,9 @@ struct HostInst {
     std::vector<double> D64;       // FP64 distances used by the initial heuristics
     std::vector<float> area, supply, demand, hu_rate, su_cap, su_fill, su_speed;
     float hu_speed = 0.f;
-    FixedPoint supq, hurq, sufq, sucq;
+    FixedPoint supq, hurq, sufq, sucq, areaq;
+    int dq_exp = 0;                // distances in fixed point: quantum 2^dq_exp
+    std::vector<int32_t> Dq;
     std::vector<long long> demq;
     std::vector<int> hu_sorted, su_sorted;
     BlobLayout L{};
@@ -130,8 +132,20 @@ int load_instance(const bl_instance &in, HostInst &h, std::string *err)
     h.hu_speed = in.hu_speed_kmh;
     int bits;
     if (!to_fixed(h.supply.data(), h.F, h.supq, &bits) || !to_fixed(h.hu_rate.data(), h.H, h.hurq, &bits) ||
-        !to_fixed(h.su_fill.data(), h.S, h.sufq, &bits) || !to_fixed(h.su_cap.data(), h.S, h.sucq, &bits))
+        !to_fixed(h.su_fill.data(), h.S, h.sufq, &bits) || !to_fixed(h.su_cap.data(), h.S, h.sucq, &bits) ||
+        !to_fixed(h.area.data(), h.F, h.areaq, &bits))
         return fail(err, BL_ETOO_LARGE, "value range too wide for exact sums");
+    // distances in fixed point: quantum 2^(e-30) with e the exponent of the largest distance, so
+    // every rounded distance is < 2^30 and a tour's sum of edges stays far below 2^63
+    {
+        float dmax = 0.f;
+        for (float d : h.D) dmax = std::max(dmax, d);
+        int e = 0;
+        std::frexp((double)std::max(dmax, 1e-30f), &e);
+        h.dq_exp = e - 30;
+        h.Dq.resize(h.D.size());
+        for (size_t k = 0; k < h.D.size(); ++k) h.Dq[k] = (int32_t)std::nearbyint(std::ldexp((double)h.D[k], -h.dq_exp));
+    }
     // Eq. 2 in fixed point: sum m_f >= ceil(d_b / 2^exp)
     long long total = 0;
     for (long long m : h.supq.m) total += m;
@@ -227,6 +241,7 @@ void build_blob(HostInst &h)
     auto take = [&](size_t bytes) { const size_t at = o; o = align_up(o + bytes, 16); return (int32_t)at; };
     BlobLayout &L = h.L;
     L.off_area = take((size_t)F * 4);
+    L.off_areaq = take((size_t)F * 8);
     L.off_supply = take((size_t)F * 4);
     L.off_supq = take((size_t)F * 8);
     L.off_demq = take((size_t)B * 8);
@@ -248,6 +263,7 @@ void build_blob(HostInst &h)
     L.total_bytes = (int32_t)o;
     h.blob.assign(o, 0);
     put(h.blob, L.off_area, h.area.data(), (size_t)F);
+    put(h.blob, L.off_areaq, h.areaq.m.data(), (size_t)F);
     put(h.blob, L.off_supply, h.supply.data(), (size_t)F);
     put(h.blob, L.off_supq, h.supq.m.data(), (size_t)F);
     put(h.blob, L.off_demq, h.demq.data(), (size_t)B);
@@ -297,7 +313,7 @@ void build_blob(HostInst &h)
     put(h.blob, L.off_hudeal_q, hq.data(), hq.size());
     put(h.blob, L.off_sudeal_m, sm.data(), sm.size());
     put(h.blob, L.off_sudeal_q, sq.data(), sq.size());
-    put(h.blob, L.off_D, h.D.data(), (size_t)N * N);
+    put(h.blob, L.off_D, h.Dq.data(), (size_t)N * N);
 }
 
 struct WsLayout {
@@ -605,16 +621,9 @@ int init_common(const bl_instance *insts, int32_t n_inst, const bl_params *param
         M.fq_scale = std::ldexp(1.0f, hi.sufq.exp);
         M.cq_scale = std::ldexp(1.0f, hi.sucq.exp);
         M.cq_scale_d = std::ldexp(1.0, hi.sucq.exp);
-        {
-            // shuttle distances in fixed point: quantum 2^(e-31) with e the exponent of the largest distance,
-            // so each rounded distance is < 2^31 and a tour's sum of n_f * d_f stays far below 2^63
-            float dmax = 0.f;
-            for (float d : hi.D) dmax = std::max(dmax, d);
-            int e = 0;
-            std::frexp((double)std::max(dmax, 1e-30f), &e);
-            M.dq_inv = std::ldexp(1.0f, 31 - e);
-            M.dq_scale = std::ldexp(1.0f, e - 31);
-        }
+        M.dq_inv = std::ldexp(1.0f, -hi.dq_exp);
+        M.dq_scale = std::ldexp(1.0f, hi.dq_exp);
+        M.aq_scale = std::ldexp(1.0f, hi.areaq.exp);
         M.L = hi.L;
         M.blob = h->at<unsigned char>(h->ws.blob[(size_t)i]);
         M.xold = h->at<int16_t>(h->ws.xold[(size_t)i]);

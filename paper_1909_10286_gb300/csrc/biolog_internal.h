@@ -15,6 +15,7 @@ namespace biolog {
 // stage only the prefix.
 struct BlobLayout {
     int32_t off_area;      // f32[F]   field sizes (ha)
+    int32_t off_areaq;     // i64[F]   field sizes in fixed point (quantum 2^area exp)
     int32_t off_supply;    // f32[F]   supplies (t)
     int32_t off_supq;      // i64[F]   supplies in fixed point (quantum 2^sup_exp)
     int32_t off_demq;      // i64[B]   smallest fixed-point supply sum meeting d_b
@@ -31,7 +32,7 @@ struct BlobLayout {
     int32_t off_sudeal_q;  // i64[T*T] their fixed-point fill sums
     int32_t off_hu_id;     // i32[H]   HU id at each sorted position
     int32_t off_su_id;     // i32[S]   SU id at each sorted position
-    int32_t off_D;         // f32[N*N] distances (km), row-major
+    int32_t off_D;         // i32[N*N] distances in fixed point: round(d * dq_inv), row-major
     int32_t prefix_bytes;  // bytes before off_D (multiple of 16)
     int32_t total_bytes;   // multiple of 16
 };
@@ -50,8 +51,9 @@ struct InstMeta {
     float fq_scale;
     float cq_scale;
     double cq_scale_d;
-    float dq_inv;              // distances -> shuttle fixed point: round(d * dq_inv)
+    float dq_inv;              // distances -> fixed point: round(d * dq_inv)
     float dq_scale;            // and back: 2^k
+    float aq_scale;            // fixed-point areas -> ha
     BlobLayout L;
     const unsigned char *blob; // device: this instance's table blob
     int16_t *xold;             // device: plan encodings (plan_len int16 each)

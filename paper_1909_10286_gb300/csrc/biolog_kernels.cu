@@ -135,7 +135,7 @@ using ShapeA = Shape<4, 0, true, 256, BIOLOG_SHAPEA_MINB>;   // <= 4 tours, <= 3
 using ShapeB = Shape<8, 1, true, 128, 4>;                     // <= 8 tours, <= 64 HUs/SUs
 using ShapeC = Shape<16, 2, false, 128, 2>;                   // <= 16 tours, <= 128 SUs, distances via L2
 
-constexpr int NF32 = 7;   // per-tour floats: LHU, LSU, A, DB2 (2 Dbar), Tc, Tw, 1/R
+constexpr int NF32 = 8;   // per-tour floats: LHU, LSU, A, DB2 (2 Dbar), Tc, Tw, 1/R, shuttle ratio
 constexpr int WQ = 64;    // per-warp queue of feasible candidates (ring buffer)
 
 template <typename M>
@@ -158,24 +158,34 @@ struct Col {
 // Instance tables and base plan as seen by one block.
 struct Ctx {
     int F, B, T, H, S, N;
-    const float *D;
+    const int *Dq;                          // fixed-point distances (dq_scale km units)
     const float *area, *supply;
+    const long long *areaq;
     const long long *supq, *demq, *hurq, *sufq, *sucq;
     const float *suinv, *sufill, *rcp;
     const int *sugrp;
     const unsigned long long *hudeal_m, *sudeal_m;
     const long long *hudeal_q, *sudeal_q;
     const int *hu_id, *su_id;
-    float inv_v, rqs, fqs, cqs, dq_inv, dq_scale;
+    float inv_v, rqs, fqs, cqs, dq_inv, dq_scale, aq_scale;
     double cqs_d;
     // base plan and derived tables (shared memory)
     const int16_t *bp_order, *tour_cnt, *field_order, *bp_cnt;
     const int16_t *tour_start, *bp_start, *field_bp, *field_pos, *bp_tour, *bp_pos;
     const long long *base_supq;
     const int8_t *bad;
-    const float *bLHU, *bLSU, *bA, *bDB2;   // base plan's route aggregates per tour
+    // base plan, per BP: first/last field node, internal HU edges, field-to-BP distances, area
+    const int16_t *bfirst, *blast;
+    const long long *bint, *bsb, *barea;
+    // base plan, per tour: HU route, SU route, area (fixed point) and 2 x mean of per-BP means
+    const long long *tLHU, *tLSU, *tA;
+    const float *tDB2;
+    const int *dqown;                      // per base field position: distance to its own BP
+    const float *kf_base;                  // base plan's shuttle ratio N_SU/sum cap per tour
+    const long long *sh_base;              // base plan's shuttle sum per tour (fixed point)
+    int memo;                              // 1 = reuse the base's shuttle sums where valid
     int nbad;
-    __device__ __forceinline__ float d(int i, int j) const { return D[i * N + j]; }
+    __device__ __forceinline__ long long dq(int i, int j) const { return (long long)Dq[i * N + j]; }
 };
 
 struct MoveRec {
@@ -296,40 +306,128 @@ struct View {
     }
 };
 
-// Route aggregates of tour g as in Fig. 1 (Sec. 2.2): HU route through the
-// fields in order, SU repositioning route, harvested area, and 2x the mean of
-// per-BP mean field-to-BP distances (Algorithm 2, Step 1). Sequential FP32
-// sums in plan order.
-struct TourAgg {
-    float LHU, LSU, A, DB2;
+// Route aggregates (Fig. 1, Sec. 2.2), exact in fixed point so that they do
+// not depend on summation order: every per-tour value is a function of the
+// tour's content only.
+//   per BP: first and last field node, the HU edges between its consecutive
+//   fields, the sum of field-to-BP distances, the harvested area;
+//   per tour: HU route HQ -> fields in order (across its BPs) -> HQ, SU route
+//   HQ -> first field of the first BP -> ... -> (previous BP -> first field of
+//   the next BP) ... -> last BP -> HQ, area, and 2 x the mean over its BPs of
+//   the mean field-to-BP distance (Algorithm 2, Step 1).
+struct BpAgg {
+    int first, last, nf;
+    long long internal, sb, area;
 };
 
-__device__ __forceinline__ TourAgg trace_tour(const Ctx &c, const View &x, int g, int nb)
+struct TourAgg {
+    long long LHU, LSU, A;
+    float DB2;
+};
+
+__device__ __forceinline__ BpAgg walk_bp(const Ctx &c, const View &x, int b)
 {
-    int prevF = 0, anchor = 0;
-    float LHU = 0.f, LSU = 0.f, A = 0.f, Dsum = 0.f;
+    BpAgg r;
+    r.nf = x.bp_len(c, b);
+    r.internal = r.sb = r.area = 0;
+    r.first = r.last = -1;
+    const int bn = 1 + b;
+    int prev = -1;
+    for (int k = 0; k < r.nf; ++k) {
+        const int f = x.field_at(c, b, k);
+        const int fn = 1 + c.B + f;
+        if (prev >= 0) r.internal += c.dq(prev, fn);
+        else r.first = fn;
+        r.sb += c.dq(fn, bn);
+        r.area += c.areaq[f];
+        prev = fn;
+    }
+    r.last = prev;
+    return r;
+}
+
+// A field reinsert (Step 8) changes two BP lists by one element each: update
+// the base aggregates from the neighbours of the removed and of the inserted
+// field instead of re-walking (exact integer arithmetic, so the result equals
+// the walk's).
+__device__ __forceinline__ BpAgg bp_agg_reinsert(const Ctx &c, const View &x, int b)
+{
+    BpAgg r;
+    r.nf = c.bp_cnt[b];
+    r.first = c.bfirst[b];
+    r.last = c.blast[b];
+    r.internal = c.bint[b];
+    r.sb = c.bsb[b];
+    r.area = c.barea[b];
+    const int st = c.bp_start[b];
+    const int vn = 1 + c.B + x.v;
+    if (b == x.sg) {   // removal at position sp
+        const int ps = x.sp;
+        const int pn = ps > 0 ? 1 + c.B + c.field_order[st + ps - 1] : -1;
+        const int nn = ps < r.nf - 1 ? 1 + c.B + c.field_order[st + ps + 1] : -1;
+        if (pn >= 0 && nn >= 0) r.internal += c.dq(pn, nn) - c.dq(pn, vn) - c.dq(vn, nn);
+        else if (pn >= 0) { r.internal -= c.dq(pn, vn); r.last = pn; }
+        else if (nn >= 0) { r.internal -= c.dq(vn, nn); r.first = nn; }
+        else { r.first = r.last = -1; }
+        r.sb -= c.dq(vn, 1 + b);
+        r.area -= c.areaq[x.v];
+        r.nf -= 1;
+    }
+    if (b == x.dg) {   // insertion at position dp of the post-removal list
+        const int len = r.nf;
+        const bool same = (b == x.sg);
+        const int dp = x.dp;
+        int an = -1, cn = -1;
+        if (dp > 0) { const int j = dp - 1; an = 1 + c.B + c.field_order[st + (same && j >= x.sp ? j + 1 : j)]; }
+        if (dp < len) { const int j = dp; cn = 1 + c.B + c.field_order[st + (same && j >= x.sp ? j + 1 : j)]; }
+        if (an >= 0 && cn >= 0) r.internal += c.dq(an, vn) + c.dq(vn, cn) - c.dq(an, cn);
+        else if (an >= 0) r.internal += c.dq(an, vn);
+        else if (cn >= 0) r.internal += c.dq(vn, cn);
+        if (dp == 0) r.first = vn;
+        if (dp == len) r.last = vn;
+        r.sb += c.dq(vn, 1 + b);
+        r.area += c.areaq[x.v];
+        r.nf += 1;
+    }
+    return r;
+}
+
+// BP b in the candidate: updated or re-walked if its field list changed, else the base's
+__device__ __forceinline__ BpAgg bp_agg(const Ctx &c, const View &x, int b)
+{
+    if (x.kind == 0 && (b == x.sg || b == x.dg)) return bp_agg_reinsert(c, x, b);
+    if (x.kind == 2 && (b == c.field_bp[x.v] || b == c.field_bp[x.w])) return walk_bp(c, x, b);
+    BpAgg r;
+    r.nf = c.bp_cnt[b];
+    r.first = c.bfirst[b];
+    r.last = c.blast[b];
+    r.internal = c.bint[b];
+    r.sb = c.bsb[b];
+    r.area = c.barea[b];
+    return r;
+}
+
+__device__ __forceinline__ TourAgg tour_agg(const Ctx &c, const View &x, int g, int nb)
+{
+    TourAgg t;
+    t.LHU = t.LSU = t.A = 0;
+    int prev_last = 0, anchor = 0, nonempty = 0;
+    float dsum = 0.f;
     for (int j = 0; j < nb; ++j) {
         const int b = x.bp_at(c, g, j);
-        const int nf = x.bp_len(c, b);
-        const int bn = 1 + b;
-        float Sb = 0.f;
-        for (int k = 0; k < nf; ++k) {
-            const int f = x.field_at(c, b, k);
-            const int fn = 1 + c.B + f;
-            LHU = __fadd_rn(LHU, c.d(prevF, fn));
-            if (k == 0) LSU = __fadd_rn(LSU, c.d(anchor, fn));
-            A = __fadd_rn(A, c.area[f]);
-            Sb = __fadd_rn(Sb, c.d(fn, bn));
-            prevF = fn;
-        }
-        Dsum = __fadd_rn(Dsum, __fmul_rn(Sb, c.rcp[nf]));
-        anchor = bn;
+        const BpAgg a = bp_agg(c, x, b);
+        if (a.nf == 0) continue;   // BPs without fields are skipped in routing
+        t.LHU += c.dq(prev_last, a.first) + a.internal;
+        t.LSU += c.dq(anchor, a.first);
+        t.A += a.area;
+        dsum = __fadd_rn(dsum, __fmul_rn(__fmul_rn(__ll2float_rn(a.sb), c.dq_scale), c.rcp[a.nf]));
+        prev_last = a.last;
+        anchor = 1 + b;
+        ++nonempty;
     }
-    TourAgg t;
-    t.LHU = __fadd_rn(LHU, c.d(prevF, 0));
-    t.LSU = __fadd_rn(LSU, c.d(anchor, 0));
-    t.A = A;
-    t.DB2 = __fmul_rn(2.0f, __fmul_rn(Dsum, c.rcp[nb]));
+    t.LHU += c.dq(prev_last, 0);
+    t.LSU += c.dq(anchor, 0);
+    t.DB2 = nonempty ? __fmul_rn(2.0f, __fmul_rn(dsum, c.rcp[nonempty])) : 0.f;
     return t;
 }
 
@@ -404,7 +502,7 @@ struct TourState {
     static constexpr int MAXT = SH::MAXT, NT = SH::NT;
     using M = typename SH::Mask;
     using S = typename SH::Sum;
-    Col<float, NT> LHU, LSU, A, DB2, Tc, Tw, iR;
+    Col<float, NT> LHU, LSU, A, DB2, Tc, Tw, iR, KF;
     Col<int, NT> star;
     Col<S, NT> Rq, Saq;
     Col<M, NT> Hm, S0;
@@ -414,7 +512,7 @@ struct TourState {
         constexpr int C = MAXT * NT;
         float *f = (float *)base + tid;
         LHU.p = f; LSU.p = f + C; A.p = f + 2 * C; DB2.p = f + 3 * C; Tc.p = f + 4 * C; Tw.p = f + 5 * C;
-        iR.p = f + 6 * C;
+        iR.p = f + 6 * C; KF.p = f + 7 * C;
         int *i = (int *)base + (size_t)NF32 * C + tid;
         star.p = i;
         S *q = (S *)((int *)base + (size_t)(NF32 + 1) * C) + tid;
@@ -447,7 +545,7 @@ __device__ ScoreOut score_candidate(const Ctx &c, const SearchParams &p, const M
     View x;
     x.set(c, m);
 
-    // --- route aggregates (Fig. 1, Sec. 2.2): trace the touched tours, reuse the base's
+    // --- route aggregates (Fig. 1, Sec. 2.2): rebuild the touched tours, reuse the base's
     const unsigned touched = x.touched(c);
     unsigned amask = 0;
     int na = 0;
@@ -456,10 +554,18 @@ __device__ ScoreOut score_candidate(const Ctx &c, const SearchParams &p, const M
         if (nb == 0) continue;
         amask |= 1u << g;
         ++na;
-        TourAgg t;
-        if ((touched >> g) & 1u) t = trace_tour(c, x, g, nb);
-        else { t.LHU = c.bLHU[g]; t.LSU = c.bLSU[g]; t.A = c.bA[g]; t.DB2 = c.bDB2[g]; }
-        ts.LHU.set(g, t.LHU); ts.LSU.set(g, t.LSU); ts.A.set(g, t.A); ts.DB2.set(g, t.DB2);
+        long long lhu, lsu, ar;
+        float db2;
+        if ((touched >> g) & 1u) {
+            const TourAgg t = tour_agg(c, x, g, nb);
+            lhu = t.LHU; lsu = t.LSU; ar = t.A; db2 = t.DB2;
+        } else {
+            lhu = c.tLHU[g]; lsu = c.tLSU[g]; ar = c.tA[g]; db2 = c.tDB2[g];
+        }
+        ts.LHU.set(g, __fmul_rn(__ll2float_rn(lhu), c.dq_scale));
+        ts.LSU.set(g, __fmul_rn(__ll2float_rn(lsu), c.dq_scale));
+        ts.A.set(g, __fmul_rn(__ll2float_rn(ar), c.aq_scale));
+        ts.DB2.set(g, db2);
     }
     const int di = (na - 1) * c.T;
     const int g_first = __ffs(amask) - 1;
@@ -633,8 +739,23 @@ __device__ ScoreOut score_candidate(const Ctx &c, const SearchParams &p, const M
             const unsigned long long s1 = (SW > 1) ? ts.S1.get(g) : 0ull;
             const int nsu = popc_m(s0) + (SW > 1 ? popc_m(s1) : 0);
             kfv[g] = __fdividef((float)nsu, __fmul_rn(__ll2float_rn(cap_sum<SH>(c, s0, s1)), c.cqs));
+            ts.KF.set(g, kfv[g]);
         }
-        if (DUMP) ts.Sh.set(g, 0ull);
+    }
+    // A tour's shuttle sum is exact and depends only on its fields, their BPs and its
+    // ratio N_SU/sum cap: if neither changed against the base plan, reuse the base's.
+    unsigned fresh = amask;
+    if (c.memo) {
+        unsigned moved = 0u;   // tours whose field -> BP content changed
+        if (x.kind == 0 && x.sg != x.dg) moved = (1u << c.bp_tour[x.sg]) | (1u << c.bp_tour[x.dg]);
+        else if (x.kind == 1 && x.sg != x.dg) moved = (1u << x.sg) | (1u << x.dg);
+        else if (x.kind == 2 && c.field_bp[x.v] != c.field_bp[x.w])
+            moved = (1u << c.bp_tour[c.field_bp[x.v]]) | (1u << c.bp_tour[c.field_bp[x.w]]);
+        else if (x.kind == 3 && c.bp_tour[x.v] != c.bp_tour[x.w]) moved = (1u << c.bp_tour[x.v]) | (1u << c.bp_tour[x.w]);
+        fresh = 0u;
+#pragma unroll
+        for (int g = 0; g < MAXT; ++g)
+            if (((amask >> g) & 1u) && (((moved >> g) & 1u) || kfv[g] != c.kf_base[g])) fresh |= 1u << g;
     }
     // rare exact path of Eq. 4: capacity sum of tour g recomputed from its SU set
     auto ceil_n = [&](int g, float sup, float kf) -> int {
@@ -647,25 +768,31 @@ __device__ ScoreOut score_candidate(const Ctx &c, const SearchParams &p, const M
         return exact_ceil(sup, nsu, (double)cap_sum<SH>(c, s0, s1) * c.cqs_d, q);
     };
     long long shq = 0;
-    for (int b = 0; b < c.B; ++b) {
-        const int g = x.tour_of_bp(c, b);
-        float kf = kfv[0];
-#pragma unroll
-        for (int t = 1; t < MAXT; ++t)
-            if (g == t) kf = kfv[t];
-        long long acc = 0;
-        const int k0 = c.bp_start[b], k1 = k0 + c.bp_cnt[b];
-        const int bn = 1 + b;
-        for (int kk = k0; kk < k1; ++kk) {
-            const int f = c.field_order[kk];
-            if (x.bp_of_field(c, f) != b) continue;   // moved to another BP: added below
-            const int n = ceil_n(g, c.supply[f], kf);
-            acc += (long long)n * __float2ll_rn(__fmul_rn(c.d(1 + c.B + f, bn), c.dq_inv));
-        }
-        shq += acc;
-        if (DUMP) ts.Sh.set(g, ts.Sh.get(g) + (unsigned long long)acc);
+    for (int g = 0; g < c.T; ++g) {
+        if (!((amask >> g) & 1u)) continue;
+        const long long v0 = ((fresh >> g) & 1u) ? 0ll : c.sh_base[g];
+        ts.Sh.set(g, (unsigned long long)v0);
+        shq += v0;
     }
-    {
+    if (fresh) {
+        for (int b = 0; b < c.B; ++b) {
+            const int g = x.tour_of_bp(c, b);
+            if (!((fresh >> g) & 1u)) continue;
+            float kf = kfv[0];
+#pragma unroll
+            for (int t = 1; t < MAXT; ++t)
+                if (g == t) kf = kfv[t];
+            long long acc = 0;
+            const int k0 = c.bp_start[b], k1 = k0 + c.bp_cnt[b];
+            for (int kk = k0; kk < k1; ++kk) {
+                const int f = c.field_order[kk];
+                if (x.bp_of_field(c, f) != b) continue;   // moved to another BP: added below
+                const int n = ceil_n(g, c.supply[f], kf);
+                acc += (long long)n * (long long)c.dqown[kk];
+            }
+            shq += acc;
+            ts.Sh.set(g, ts.Sh.get(g) + (unsigned long long)acc);
+        }
         int mv_f0 = -1, mv_f1 = -1;
         if (x.kind == 0 && x.sg != x.dg) mv_f0 = x.v;
         if (x.kind == 2 && c.field_bp[x.v] != c.field_bp[x.w]) { mv_f0 = x.v; mv_f1 = x.w; }
@@ -680,9 +807,9 @@ __device__ ScoreOut score_candidate(const Ctx &c, const SearchParams &p, const M
                 for (int t = 1; t < MAXT; ++t)
                     if (g == t) kf = kfv[t];
                 const int n = ceil_n(g, c.supply[f], kf);
-                const long long a = (long long)n * __float2ll_rn(__fmul_rn(c.d(1 + c.B + f, 1 + b), c.dq_inv));
+                const long long a = (long long)n * c.dq(1 + c.B + f, 1 + b);
                 shq += a;
-                if (DUMP) ts.Sh.set(g, ts.Sh.get(g) + (unsigned long long)a);
+                ts.Sh.set(g, ts.Sh.get(g) + (unsigned long long)a);
             }
         }
     }
@@ -698,6 +825,7 @@ __device__ ScoreOut score_candidate(const Ctx &c, const SearchParams &p, const M
         cost = __fadd_rn(cost, route);
         if (DUMP) {
             const float shuttle = __fmul_rn(__fmul_rn(__ll2float_rn((long long)ts.Sh.get(g)), c.dq_scale), 2.0f);
+            (void)shuttle;
             if (o_nhu) o_nhu[g] = (int16_t)nhu;
             if (o_nsu) o_nsu[g] = (int16_t)nsu;
             if (o_tc) o_tc[g] = ts.Tc.get(g);
@@ -745,7 +873,8 @@ __host__ __device__ inline SmemPlan carve(size_t tour_bytes, int threads, int ma
     s.off_derived = o; o += align16((size_t)(max_T + 3 * max_B + 2 * max_F) * 2);
     s.off_supq = o; o += align16((size_t)max_B * 8);
     s.off_bad = o; o += align16((size_t)max_B);
-    s.off_base_agg = o; o += align16((size_t)4 * max_T * 4);
+    s.off_base_agg = o; o += align16((size_t)max_B * 3 * 8 + (size_t)max_T * (3 * 8 + 4 + 4) + (size_t)max_T * 8 +
+                                     (size_t)max_F * 4 + (size_t)max_B * 2 * 2);
     s.off_tour = o; o += align16(tour_bytes);
     s.off_qidx = o; o += align16((size_t)(threads / 32) * WQ * 4);
     s.off_qmv = o; o += align16((size_t)(threads / 32) * WQ * 8);
@@ -814,8 +943,9 @@ __device__ bool stage_instance(const InstMeta &M, BlockShared &bs, unsigned char
     }
     const unsigned char *blob = smem + sp.off_blob;
     c.F = M.F; c.B = M.B; c.T = M.T; c.H = M.H; c.S = M.S; c.N = M.N;
-    c.D = SH::DSM ? (const float *)(blob + M.L.off_D) : (const float *)(M.blob + M.L.off_D);
+    c.Dq = SH::DSM ? (const int *)(blob + M.L.off_D) : (const int *)(M.blob + M.L.off_D);
     c.area = (const float *)(blob + M.L.off_area);
+    c.areaq = (const long long *)(blob + M.L.off_areaq);
     c.supply = (const float *)(blob + M.L.off_supply);
     c.supq = (const long long *)(blob + M.L.off_supq);
     c.demq = (const long long *)(blob + M.L.off_demq);
@@ -833,7 +963,7 @@ __device__ bool stage_instance(const InstMeta &M, BlockShared &bs, unsigned char
     c.hu_id = (const int *)(blob + M.L.off_hu_id);
     c.su_id = (const int *)(blob + M.L.off_su_id);
     c.inv_v = M.inv_hu_speed; c.rqs = M.rq_scale; c.fqs = M.fq_scale; c.cqs = M.cq_scale; c.cqs_d = M.cq_scale_d;
-    c.dq_inv = M.dq_inv; c.dq_scale = M.dq_scale;
+    c.dq_inv = M.dq_inv; c.dq_scale = M.dq_scale; c.aq_scale = M.aq_scale;
     const int B = M.B, T = M.T, F = M.F;
     c.bp_order = plan;
     c.tour_cnt = plan + B;
@@ -844,10 +974,18 @@ __device__ bool stage_instance(const InstMeta &M, BlockShared &bs, unsigned char
     int16_t *field_bp = der + T + 3 * B, *field_pos = der + T + 3 * B + F;
     long long *base_supq = (long long *)(smem + sp.off_supq);
     int8_t *bad = (int8_t *)(smem + sp.off_bad);
-    float *agg = (float *)(smem + sp.off_base_agg);
+    unsigned char *bt = smem + sp.off_base_agg;   // base per-BP and per-tour tables
+    long long *bint = (long long *)bt, *bsb = bint + B, *barea = bsb + B;
+    long long *tLHU = barea + B, *tLSU = tLHU + T, *tA = tLSU + T;
+    float *tDB2 = (float *)(tA + T);
+    float *kf_base = tDB2 + T;
+    long long *sh_base = (long long *)(bt + (size_t)B * 3 * 8 + (size_t)T * (3 * 8 + 4 + 4));
+    int *dqown = (int *)(sh_base + T);
+    int16_t *bfirst = (int16_t *)(dqown + F), *blast = bfirst + B;
     c.tour_start = tour_start; c.bp_start = bp_start; c.bp_tour = bp_tour; c.bp_pos = bp_pos;
     c.field_bp = field_bp; c.field_pos = field_pos; c.base_supq = base_supq; c.bad = bad;
-    c.bLHU = agg; c.bLSU = agg + T; c.bA = agg + 2 * T; c.bDB2 = agg + 3 * T;
+    c.bint = bint; c.bsb = bsb; c.barea = barea; c.tLHU = tLHU; c.tLSU = tLSU; c.tA = tA; c.tDB2 = tDB2;
+    c.dqown = dqown; c.bfirst = bfirst; c.blast = blast; c.kf_base = kf_base; c.sh_base = sh_base; c.memo = 0;
     if (tid == 0) {
         int s = 0;
         for (int g = 0; g < T; ++g) { tour_start[g] = (int16_t)s; s += c.tour_cnt[g]; }
@@ -866,6 +1004,7 @@ __device__ bool stage_instance(const InstMeta &M, BlockShared &bs, unsigned char
             const int f = c.field_order[bp_start[b] + k];
             field_bp[f] = (int16_t)b; field_pos[f] = (int16_t)k;
             s += c.supq[f];
+            dqown[bp_start[b] + k] = c.Dq[(1 + B + f) * c.N + 1 + b];
         }
         base_supq[b] = s;
         bad[b] = (int8_t)(s < c.demq[b] ? 1 : 0);
@@ -876,18 +1015,40 @@ __device__ bool stage_instance(const InstMeta &M, BlockShared &bs, unsigned char
         for (int b = 0; b < B; ++b) nb += bad[b];
         bs.nbad = nb;
     }
-    // base plan's tour aggregates, traced with the same code as candidates
+    // base plan's per-BP aggregates, then per-tour aggregates, with the same code as candidates
+    View idv;
+    idv.kind = 4; idv.v = idv.w = idv.sg = idv.sp = idv.dg = idv.dp = -1;
+    for (int b = tid; b < B; b += nt) {
+        const BpAgg a = walk_bp(c, idv, b);
+        bfirst[b] = (int16_t)a.first; blast[b] = (int16_t)a.last;
+        bint[b] = a.internal; bsb[b] = a.sb; barea[b] = a.area;
+    }
+    __syncthreads();
     for (int g = tid; g < T; g += nt) {
-        View x;
-        x.kind = 4; x.v = x.w = x.sg = x.sp = x.dg = x.dp = -1;
         const int nb = c.tour_cnt[g];
         TourAgg t;
-        t.LHU = t.LSU = t.A = t.DB2 = 0.f;
-        if (nb > 0) t = trace_tour(c, x, g, nb);
-        agg[g] = t.LHU; agg[T + g] = t.LSU; agg[2 * T + g] = t.A; agg[3 * T + g] = t.DB2;
+        t.LHU = t.LSU = t.A = 0; t.DB2 = 0.f;
+        if (nb > 0) t = tour_agg(c, idv, g, nb);
+        tLHU[g] = t.LHU; tLSU[g] = t.LSU; tA[g] = t.A; tDB2[g] = t.DB2;
+    }
+    __syncthreads();
+    // the base plan's own shuttle ratios and sums per tour, scored with the candidates' code
+    if (tid == 0) {
+        c.nbad = bs.nbad;
+        for (int g = 0; g < T; ++g) { kf_base[g] = 0.f; sh_base[g] = 0; }
+        if (bs.nbad == 0) {
+            const MoveRec idm = {4, 0, 0, 0};
+            score_candidate<SH, false>(c, p, idm, __int_as_float(0x7f800000), smem + sp.off_tour, tid, nullptr,
+                                       nullptr, nullptr, nullptr, nullptr, nullptr, nullptr);
+            TourState<SH> ts;
+            ts.bind(smem + sp.off_tour, tid);
+            for (int g = 0; g < T; ++g)
+                if (c.tour_cnt[g] > 0) { kf_base[g] = ts.KF.get(g); sh_base[g] = (long long)ts.Sh.get(g); }
+        }
     }
     __syncthreads();
     c.nbad = bs.nbad;
+    c.memo = 1;
     return true;
 }
 
