@@ -36,6 +36,8 @@ sys.path.insert(0, ROOT)
 METRIC = "candidates scored/s; time to reach within 1% of best cost (learned+batched vs plain)"
 UNIT = "candidates/s"
 WORKLOAD = "paper-scale plain search: 40 fields, 5 BPs, 3 tours, 10 HUs, 20 SUs, 50x50 km, 2^20 candidates/iter"
+WORKLOAD_BATCHED = ("batched uneven instances: 256 instances (fields U{10..120}, BPs U{2..10}, tours U{1..6}, "
+                    "HUs U{2..20}, SUs U{4..40}), 2^16 candidates/instance/iter, one launch per iteration")
 L2_FLUSH_BYTES = 256 << 20
 
 
@@ -194,6 +196,8 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=20)
     ap.add_argument("--cpu-budget", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--n-inst", type=int, default=256, help="instances of the batched workload")
+    ap.add_argument("--no-autotune", action="store_true")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     ws, rank, local = _dist()
@@ -209,10 +213,24 @@ def main():
 
     torch.cuda.set_device(local)
     n = args.n_cand or I.SEARCH[args.workload][0]
-    inst = I.make_instance(args.workload, args.seed + rank)
     kw = dict(eps=0.5, seed=1000 + args.seed + rank, gate=1)
     stream = torch.cuda.Stream()
-    S = biolog.Search([inst], biolog.make_params(n_cand=n, **kw), stream=stream)
+    tuned = None
+    if args.workload == "batched":
+        insts = I.make_batch("batched", range(args.seed * 1000 + rank * args.n_inst,
+                                             args.seed * 1000 + (rank + 1) * args.n_inst))
+        if args.no_autotune:
+            params = biolog.make_params(n_cand=n, **kw)
+        else:
+            from paper_1909_10286_gb300 import autotune
+            tuned = autotune.tune(insts, n, base_params=kw)
+            params = biolog.make_params(n_cand=n, blocks_per_sm=tuned["blocks_per_sm"], tile=tuned["tile"], **kw)
+    else:
+        insts = [I.make_instance(args.workload, args.seed + rank)]
+        params = biolog.make_params(n_cand=n, **kw)
+    inst = insts[0]
+    n_total = n * len(insts)
+    S = biolog.Search(insts, params, stream=stream)
     cfg = S.config()
     with torch.cuda.stream(stream):
         S.search_step(args.warmup)
@@ -234,7 +252,7 @@ def main():
     clk = clocks.stop()
     t_ms = sum(a.elapsed_time(b) for a, b in evs)
     t_ms = _max_over_ranks(t_ms, ws)
-    value = n * args.steps * ws / (t_ms / 1e3)
+    value = n_total * args.steps * ws / (t_ms / 1e3)
     ms_step = t_ms / args.steps
 
     # e2e through the C ABI: state in from pinned host memory, one iteration, state out
@@ -255,15 +273,16 @@ def main():
                 dst[...] = src
         hstate.update(cstar=out["cstar"], tmaxstar=out["tmaxstar"], iter=out["iter"])
     e2e_s = _max_over_ranks(time.perf_counter() - t0, ws)
-    e2e = {"value": n * args.e2e_steps * ws / e2e_s, "unit": UNIT, "h2d_bytes_per_step": bytes_state,
+    e2e = {"value": n_total * args.e2e_steps * ws / e2e_s, "unit": UNIT, "h2d_bytes_per_step": bytes_state,
            "d2h_bytes_per_step": bytes_state,
            "api": "bl_set_state + bl_search_step(1) + bl_get_state, pinned host buffers"}
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": WORKLOAD if args.workload == "paper" else args.workload,
-                       "instance_seed": args.seed, "n_cand_per_iter": n, "eps": 0.5, "gate": 1,
+            "config": {"workload": {"paper": WORKLOAD, "batched": WORKLOAD_BATCHED}.get(args.workload, args.workload),
+                       "instance_seed": args.seed, "n_instances": len(insts), "n_cand_per_iter": n_total,
+                       "eps": 0.5, "gate": 1, "autotuned": tuned,
                        "l2": "flushed before every timed step (256 MiB device write)",
                        "kernel": cfg, "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU"},
             "gpu_launches": args.steps * cfg["launches_per_iter"], "clocks": clk, "e2e": e2e}
@@ -284,11 +303,13 @@ def main():
         f_mhz = float(peaks.get("sm_max_mhz", 2070.0))
         sms = torch.cuda.get_device_properties(local).multi_processor_count
         peak = sms * 4 * 32 * f_mhz * 1e6 / 1e12            # lane-ops/s: 4 schedulers x 32 lanes per SM
-        achieved = w_per * n / (ms_step / 1e3) / 1e12
+        achieved = w_per * n_total / (ms_step / 1e3) / 1e12
         line["roofline"] = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tlane-op/s",
                             "frac": achieved / peak, "traffic": None, "ops_per_candidate": w_per,
                             "peak_basis": f"{sms} SMs x 4 schedulers x 32 lanes x {f_mhz:.0f} MHz (sm_max_mhz of "
                                           "MEASURED_PEAKS.json)"}
+        if len(insts) > 1:
+            line["roofline"]["ops_per_candidate_basis"] = "oracle count on instance 0 of the batch"
         if ws == 1 and not args.no_cpu_baseline:
             rate, m_s, iters, thr = oracle_throughput(inst, kw, n, args.cpu_budget, os.cpu_count() or 1)
             line["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": thr, "kind": "oracle",

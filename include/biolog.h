@@ -217,6 +217,51 @@ int bl_decode_candidates(bl_handle *h, int32_t inst, int32_t use_best, uint32_t 
 int bl_argmin_noalloc(bl_handle *h, int32_t inst, int32_t use_best, uint32_t iter, float tmax_star, int32_t i0,
                       int32_t n, uint64_t *d_key, float *d_tmax);
 
+/* ---- Learned move ranking (an extension; the paper draws moves uniformly) ----
+   A small MLP in -> H -> H -> H -> 1 with ReLU scores candidate moves from
+   per-move features (bl_features); its GEMMs run on the tensor cores in BF16
+   with FP32 accumulation (tcgen05, accumulators in tensor memory); master
+   weights are FP32; training minimises the mean squared error with Adam. All
+   pointers named d_* are device memory owned by the caller; calls are
+   asynchronous on the MLP's stream unless they return host values. */
+typedef struct bl_mlp bl_mlp;
+
+/* Create an MLP with He-uniform initial weights drawn from `seed`. in_dim in
+   [1, 256], hidden a multiple of 16 in [16, 256], max_batch the largest M of
+   later calls. Owns its device memory. */
+int bl_mlp_create(int32_t in_dim, int32_t hidden, int32_t max_batch, uint64_t seed, void *cuda_stream, bl_mlp **out);
+
+/* y[M] = MLP(x[M x in_dim]), x BF16 row-major. */
+int bl_mlp_forward(bl_mlp *m, const uint16_t *d_x, int32_t M, float *d_y);
+
+/* Forward and backward pass of the loss mean_i (y_i - t_i)^2 without
+   updating; the gradients are then readable with bl_mlp_get(which = 1).
+   Synchronises; *h_loss (may be NULL) receives the loss. */
+int bl_mlp_grads(bl_mlp *m, const uint16_t *d_x, const float *d_target, int32_t M, float *h_loss);
+
+/* One Adam step (beta 0.9 / 0.999) with learning rate lr on that loss. */
+int bl_mlp_train_step(bl_mlp *m, const uint16_t *d_x, const float *d_target, int32_t M, float lr, float *h_loss);
+
+/* Copy parameters (which = 0) or the last gradients (which = 1) to host
+   buffers: w1 [H x in], b1 [H], w2 [H x H], b2 [H], w3 [H x H], b3 [H],
+   w4 [H], b4 [1]; NULL pointers are skipped. Synchronises. */
+int bl_mlp_get(bl_mlp *m, int32_t which, float *w1, float *b1, float *w2, float *b2, float *w3, float *b3, float *w4,
+               float *b4);
+
+/* Replace the parameters (host buffers, same layout). */
+int bl_mlp_set(bl_mlp *m, const float *w1, const float *b1, const float *w2, const float *b2, const float *w3,
+               const float *b3, const float *w4, const float *b4);
+
+int bl_mlp_free(bl_mlp *m);
+const char *bl_mlp_last_error(const bl_mlp *m);
+
+/* The tensor-core GEMM itself: C[M x N] = A[M x K] B[N x K]^T (+ bias[N])
+   (ReLU if relu), A and B BF16 row-major, C as FP32 (d_cf) and/or BF16
+   (d_cb); 1 <= N <= 256. *d_err becomes nonzero if a bounded wait on the
+   tensor cores gave up. */
+int bl_gemm_bf16(const uint16_t *d_a, const uint16_t *d_b, const float *d_bias, float *d_cf, uint16_t *d_cb, int32_t M,
+                 int32_t N, int32_t K, int32_t relu, uint32_t *d_err, void *cuda_stream);
+
 /* Kernel configuration in use: threads per block, grid blocks, candidates
    per work item, and the number of kernels one iteration launches. */
 int bl_get_config(bl_handle *h, int32_t *block_threads, int32_t *grid_blocks, int32_t *tile,

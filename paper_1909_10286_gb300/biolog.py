@@ -24,7 +24,9 @@ _lock = threading.Lock()
 BL_OK, BL_EINVAL, BL_EINFEASIBLE_INSTANCE, BL_ETOO_LARGE, BL_ECUDA, BL_ETIMEOUT, BL_ESTATE = 0, -1, -2, -3, -4, -5, -6
 EXPORTS = ("bl_workspace_bytes", "bl_plan_init", "bl_plan_init_batch", "bl_search_step", "bl_best_plan",
            "bl_get_state", "bl_set_state", "bl_get_log", "bl_score_candidates", "bl_decode_candidates",
-           "bl_get_config", "bl_plan_free", "bl_last_error", "bl_global_error", "bl_argmin_noalloc")
+           "bl_get_config", "bl_plan_free", "bl_last_error", "bl_global_error", "bl_argmin_noalloc",
+           "bl_mlp_create", "bl_mlp_forward", "bl_mlp_grads", "bl_mlp_train_step", "bl_mlp_get", "bl_mlp_set",
+           "bl_mlp_free", "bl_mlp_last_error", "bl_gemm_bf16")
 
 
 class BiologError(RuntimeError):

@@ -17,7 +17,7 @@ CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_lib")
 LIB = os.path.join(OUT, "libbiolog.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["biolog_kernels.cu", "biolog_host.cpp"]
+SOURCES = ["biolog_kernels.cu", "biolog_host.cpp", "biolog_mlp.cu", "biolog_mlp_host.cpp"]
 HEADERS = [os.path.join(CSRC, "biolog_internal.h"), os.path.join(ROOT, "include", "biolog.h")]
 
 

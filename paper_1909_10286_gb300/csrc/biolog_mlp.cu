@@ -1,0 +1,381 @@
+// Tensor-core kernels of the learned move ranking: a BF16 GEMM on the 5th
+// generation tensor cores (tcgen05.mma, FP32 accumulators in tensor memory),
+// plus the small elementwise kernels of the MLP's forward pass, backward pass
+// and Adam update. Nothing here is from the paper (the learned proposal is an
+// extension of its random Step 8).
+//
+// GEMM: C[M x N] = A[M x K] * B[N x K]^T (+ bias[N], optional ReLU), A and B
+// BF16 row-major with K contiguous, C written as FP32 and/or BF16. One CTA of
+// 128 threads per 128-row tile and the whole N (<= 256): the accumulator tile
+// is 128 TMEM lanes x N FP32 columns. K is staged in chunks of 64 into shared
+// memory in the canonical no-swizzle K-major layout -- each 16-wide K slice a
+// slab of 8x8 core matrices, (row group, k block) at offset (2 * rg + kb) * 128
+// bytes -- and one elected thread issues one tcgen05.mma per slice, committed
+// to an mbarrier that the CTA waits on with a wall-clock bound.
+#include <cstdint>
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+namespace biolog {
+
+namespace mlp {
+
+constexpr int BM = 128;        // rows per CTA (TMEM lanes)
+constexpr int BK = 64;         // K per staged chunk
+constexpr int THREADS = 128;   // 4 warps: warp w owns TMEM lanes 32w..32w+31
+constexpr int TMEM_COLS = 256;
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ uint64_t now_ns()
+{
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ bool mbar_try(uint64_t *bar, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// wait for the MMAs committed to `bar`; gives up after ~1 s
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity)
+{
+    if (mbar_try(bar, parity)) return true;
+    const uint64_t t0 = now_ns();
+    while (!mbar_try(bar, parity))
+        if (now_ns() - t0 > 1000000000ull) return false;
+    return true;
+}
+
+// Shared-memory matrix descriptor (no swizzle, K-major): start address, byte
+// offset between core matrices adjacent in K (leading) and in M/N (stride),
+// descriptor version 1.
+__device__ __forceinline__ uint64_t smem_desc(const void *p, uint32_t lbo, uint32_t sbo)
+{
+    uint64_t d = 0;
+    d |= (uint64_t)((smem_u32(p) >> 4) & 0x3FFFu);
+    d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;
+    d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
+    d |= (uint64_t)1 << 46;
+    return d;
+}
+
+// Instruction descriptor of kind::f16: FP32 accumulator, BF16 A and B, both K-major.
+__host__ __device__ constexpr uint32_t instr_desc(int m, int n)
+{
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(m >> 4) << 24);
+}
+
+// Copy a [rows x 64] BF16 chunk (row stride ld elements, starting at column k0)
+// into 4 slabs of 16 K each; rows >= nrows and columns >= K are zero.
+__device__ __forceinline__ void stage_chunk(__nv_bfloat16 *dst, const __nv_bfloat16 *src, int rows, int nrows, int ld,
+                                            int k0, int K)
+{
+    // one 16-byte segment = one core-matrix row: 8 consecutive K elements
+    const int segs = rows * (BK / 8);
+    for (int s = threadIdx.x; s < segs; s += blockDim.x) {
+        const int r = s / (BK / 8);
+        const int kb = s % (BK / 8);          // k block within the chunk (0..7)
+        const int slab = kb >> 1, kin = kb & 1;
+        uint4 v = make_uint4(0u, 0u, 0u, 0u);
+        const int k = k0 + kb * 8;
+        if (r < nrows && k < K) {
+            if (k + 8 <= K && ((ld & 7) == 0)) {
+                v = *reinterpret_cast<const uint4 *>(src + (size_t)r * ld + k);
+            } else {
+                __nv_bfloat16 tmp[8];
+                for (int e = 0; e < 8; ++e)
+                    tmp[e] = (k + e < K) ? src[(size_t)r * ld + k + e] : __float2bfloat16(0.f);
+                v = *reinterpret_cast<uint4 *>(tmp);
+            }
+        }
+        // slab layout: slab s holds rows x 16 elements; core matrix (rg, kin) at (2*rg + kin)*128 bytes
+        unsigned char *base = reinterpret_cast<unsigned char *>(dst) + (size_t)slab * rows * 32;
+        *reinterpret_cast<uint4 *>(base + (size_t)((r >> 3) * 2 + kin) * 128 + (r & 7) * 16) = v;
+    }
+}
+
+__global__ void __launch_bounds__(THREADS, 1)
+gemm_bf16_tn_kernel(const __nv_bfloat16 *__restrict__ A, const __nv_bfloat16 *__restrict__ B,
+                    const float *__restrict__ bias, float *__restrict__ Cf, __nv_bfloat16 *__restrict__ Cb,
+                    int M, int N, int K, int relu, unsigned int *__restrict__ err)
+{
+    extern __shared__ __align__(1024) unsigned char smem[];
+    __shared__ uint64_t mbar;
+    __shared__ uint32_t tmem_base_sh;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int m0 = blockIdx.x * BM;
+    const int Np = (N + 15) & ~15;   // MMA N, a multiple of 16
+    __nv_bfloat16 *As = reinterpret_cast<__nv_bfloat16 *>(smem);
+    __nv_bfloat16 *Bs = As + BM * BK;
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base_sh)),
+                     "r"(TMEM_COLS)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    if (tid == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&mbar)) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = tmem_base_sh;
+    const uint32_t idesc = instr_desc(BM, Np);
+    uint32_t phase = 0;
+    bool ok = true;
+    for (int k0 = 0; k0 < K; k0 += BK) {
+        stage_chunk(As, A + (size_t)m0 * K, BM, min(BM, M - m0), K, k0, K);
+        stage_chunk(Bs, B, Np, N, K, k0, K);
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");   // generic writes -> tensor-core reads
+        __syncthreads();
+        if (tid == 0) {
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            for (int s = 0; s < BK / 16; ++s) {
+                if (k0 + s * 16 >= K) break;
+                const uint64_t ad = smem_desc(reinterpret_cast<unsigned char *>(As) + (size_t)s * BM * 32, 128, 256);
+                const uint64_t bd = smem_desc(reinterpret_cast<unsigned char *>(Bs) + (size_t)s * Np * 32, 128, 256);
+                const uint32_t acc = (k0 > 0 || s > 0) ? 1u : 0u;
+                asm volatile(
+                    "{\n\t.reg .pred p;\n\t"
+                    "setp.ne.b32 p, %4, 0;\n\t"
+                    "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem),
+                    "l"(ad), "l"(bd), "r"(idesc), "r"(acc)
+                    : "memory");
+            }
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                             smem_u32(&mbar))
+                         : "memory");
+        }
+        // every thread waits for this chunk's MMAs before the buffers are overwritten
+        const bool done = mbar_wait(&mbar, phase);
+        phase ^= 1u;
+        ok = __syncthreads_and(done ? 1 : 0) != 0;
+        if (!ok) break;
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    }
+    if (ok) {
+        // epilogue: thread (warp w, lane l) owns row 32w + l of the tile
+        const int row = m0 + warp * 32 + lane;
+        const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16);
+        for (int c0 = 0; c0 < Np; c0 += 16) {
+            uint32_t v[16];
+            asm volatile(
+                "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+                : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+                  "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]),
+                  "=r"(v[15])
+                : "r"(taddr + (uint32_t)c0));
+            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+            if (row < M) {
+#pragma unroll
+                for (int j = 0; j < 16; ++j) {
+                    const int col = c0 + j;
+                    if (col >= N) break;
+                    float x = __uint_as_float(v[j]);
+                    if (bias) x += bias[col];
+                    if (relu) x = fmaxf(x, 0.f);
+                    if (Cf) Cf[(size_t)row * N + col] = x;
+                    if (Cb) Cb[(size_t)row * N + col] = __float2bfloat16(x);
+                }
+            }
+        }
+    } else {
+        if (tid == 0) atomicExch(err, 1u);
+        mbar_wait(&mbar, phase ^ 1u);   // give MMAs still in flight a second bounded chance before freeing TMEM
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS) : "memory");
+}
+
+// ---- elementwise kernels of the MLP ---------------------------------------
+__global__ void transpose_bf16_kernel(const __nv_bfloat16 *__restrict__ in, __nv_bfloat16 *__restrict__ out, int R,
+                                      int Cn)
+{
+    __shared__ __nv_bfloat16 t[32][33];
+    const int c = blockIdx.x * 32 + threadIdx.x, r0 = blockIdx.y * 32;
+    for (int j = threadIdx.y; j < 32; j += blockDim.y) {
+        const int r = r0 + j;
+        t[j][threadIdx.x] = (r < R && c < Cn) ? in[(size_t)r * Cn + c] : __float2bfloat16(0.f);
+    }
+    __syncthreads();
+    const int oc = r0 + threadIdx.x;
+    for (int j = threadIdx.y; j < 32; j += blockDim.y) {
+        const int orow = blockIdx.x * 32 + j;
+        if (orow < Cn && oc < R) out[(size_t)orow * R + oc] = t[threadIdx.x][j];
+    }
+}
+
+// output layer y = h . w + b (one warp per row) and the MSE gradient dy = 2 (y - t) / M
+__global__ void head_forward_kernel(const __nv_bfloat16 *__restrict__ h, const float *__restrict__ w, const float *b,
+                                    float *__restrict__ y, const float *__restrict__ target, float *__restrict__ dy,
+                                    float *__restrict__ loss, int M, int H)
+{
+    const int row = blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32, lane = threadIdx.x & 31;
+    if (row >= M) return;
+    float s = 0.f;
+    for (int j = lane; j < H; j += 32) s = fmaf(__bfloat162float(h[(size_t)row * H + j]), w[j], s);
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    s += b[0];
+    if (lane == 0) {
+        y[row] = s;
+        if (target) {
+            const float e = s - target[row];
+            dy[row] = 2.f * e / (float)M;
+            atomicAdd(loss, e * e / (float)M);
+        }
+    }
+}
+
+// dh = dy (outer) w, masked by h > 0 (ReLU of the layer below); dw = h^T dy, db = sum dy
+__global__ void head_backward_kernel(const __nv_bfloat16 *__restrict__ h, const float *__restrict__ w,
+                                     const float *__restrict__ dy, __nv_bfloat16 *__restrict__ dz, float *__restrict__ dw,
+                                     float *__restrict__ db, int M, int H)
+{
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j < H) {
+        float acc = 0.f;
+        for (int m = 0; m < M; ++m) acc = fmaf(__bfloat162float(h[(size_t)m * H + j]), dy[m], acc);
+        dw[j] = acc;
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        float s = 0.f;
+        for (int m = 0; m < M; ++m) s += dy[m];
+        db[0] = s;
+    }
+    for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < M * H; idx += gridDim.x * blockDim.x) {
+        const int m = idx / H, jj = idx % H;
+        const float hv = __bfloat162float(h[idx]);
+        dz[idx] = __float2bfloat16(hv > 0.f ? dy[m] * w[jj] : 0.f);
+    }
+}
+
+// dz = dh * (h > 0), in place on BF16 (ReLU backward), and db[j] = sum_m dz
+__global__ void relu_backward_kernel(__nv_bfloat16 *__restrict__ dh, const __nv_bfloat16 *__restrict__ h, int M, int H)
+{
+    for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < M * H; idx += gridDim.x * blockDim.x)
+        if (!(__bfloat162float(h[idx]) > 0.f)) dh[idx] = __float2bfloat16(0.f);
+}
+
+__global__ void colsum_kernel(const __nv_bfloat16 *__restrict__ x, float *__restrict__ out, int M, int H)
+{
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= H) return;
+    float s = 0.f;
+    for (int m = 0; m < M; ++m) s += __bfloat162float(x[(size_t)m * H + j]);
+    out[j] = s;
+}
+
+// Adam on FP32 master weights; the BF16 copy used by the GEMMs is refreshed
+__global__ void adam_kernel(float *__restrict__ w, __nv_bfloat16 *__restrict__ wb, const float *__restrict__ g,
+                            float *__restrict__ m, float *__restrict__ v, int n, float lr, float b1, float b2, float eps,
+                            float c1, float c2)
+{
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const float gi = g[i];
+        const float mi = b1 * m[i] + (1.f - b1) * gi;
+        const float vi = b2 * v[i] + (1.f - b2) * gi * gi;
+        m[i] = mi;
+        v[i] = vi;
+        const float wi = w[i] - lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+        w[i] = wi;
+        if (wb) wb[i] = __float2bfloat16(wi);
+    }
+}
+
+__global__ void f32_to_bf16_kernel(const float *__restrict__ x, __nv_bfloat16 *__restrict__ y, int n)
+{
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) y[i] = __float2bfloat16(x[i]);
+}
+
+}  // namespace mlp
+
+// at least 80 KB, so no more than two CTAs (2 x 256 TMEM columns) are resident on one SM
+// and the tensor-memory allocation never has to wait
+size_t mlp_gemm_smem(int N)
+{
+    const size_t need = (size_t)mlp::BM * mlp::BK * 2 + (size_t)((N + 15) & ~15) * mlp::BK * 2 + 1024;
+    return need > 80 * 1024 ? need : 80 * 1024;
+}
+
+cudaError_t launch_gemm_bf16(const void *A, const void *B, const float *bias, float *Cf, void *Cb, int M, int N, int K,
+                             int relu, unsigned int *err, cudaStream_t s)
+{
+    const size_t smem = mlp_gemm_smem(N);
+    cudaError_t e = cudaFuncSetAttribute(mlp::gemm_bf16_tn_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    const int grid = (M + mlp::BM - 1) / mlp::BM;
+    mlp::gemm_bf16_tn_kernel<<<grid, mlp::THREADS, smem, s>>>(
+        reinterpret_cast<const __nv_bfloat16 *>(A), reinterpret_cast<const __nv_bfloat16 *>(B), bias, Cf,
+        reinterpret_cast<__nv_bfloat16 *>(Cb), M, N, K, relu, err);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_transpose_bf16(const void *in, void *out, int R, int Cn, cudaStream_t s)
+{
+    dim3 grid((Cn + 31) / 32, (R + 31) / 32), block(32, 8);
+    mlp::transpose_bf16_kernel<<<grid, block, 0, s>>>(reinterpret_cast<const __nv_bfloat16 *>(in),
+                                                      reinterpret_cast<__nv_bfloat16 *>(out), R, Cn);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_head_forward(const void *h, const float *w, const float *b, float *y, const float *target, float *dy,
+                                float *loss, int M, int H, cudaStream_t s)
+{
+    const int rows_per_block = 8;
+    mlp::head_forward_kernel<<<(M + rows_per_block - 1) / rows_per_block, 32 * rows_per_block, 0, s>>>(
+        reinterpret_cast<const __nv_bfloat16 *>(h), w, b, y, target, dy, loss, M, H);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_head_backward(const void *h, const float *w, const float *dy, void *dz, float *dw, float *db, int M,
+                                 int H, cudaStream_t s)
+{
+    mlp::head_backward_kernel<<<(H + 127) / 128, 128, 0, s>>>(reinterpret_cast<const __nv_bfloat16 *>(h), w, dy,
+                                                              reinterpret_cast<__nv_bfloat16 *>(dz), dw, db, M, H);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_relu_backward(void *dh, const void *h, int M, int H, cudaStream_t s)
+{
+    mlp::relu_backward_kernel<<<1024, 256, 0, s>>>(reinterpret_cast<__nv_bfloat16 *>(dh),
+                                                   reinterpret_cast<const __nv_bfloat16 *>(h), M, H);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_colsum(const void *x, float *out, int M, int H, cudaStream_t s)
+{
+    mlp::colsum_kernel<<<(H + 127) / 128, 128, 0, s>>>(reinterpret_cast<const __nv_bfloat16 *>(x), out, M, H);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_adam(float *w, void *wb, const float *g, float *m, float *v, int n, float lr, float b1, float b2,
+                        float eps, int step, cudaStream_t s)
+{
+    float c1 = 1.f, c2 = 1.f;
+    for (int i = 0; i < step; ++i) { c1 *= b1; c2 *= b2; }
+    mlp::adam_kernel<<<256, 256, 0, s>>>(w, reinterpret_cast<__nv_bfloat16 *>(wb), g, m, v, n, lr, b1, b2, eps,
+                                         1.f - c1, 1.f - c2);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_f32_to_bf16(const float *x, void *y, int n, cudaStream_t s)
+{
+    mlp::f32_to_bf16_kernel<<<256, 256, 0, s>>>(x, reinterpret_cast<__nv_bfloat16 *>(y), n);
+    return cudaGetLastError();
+}
+
+}  // namespace biolog

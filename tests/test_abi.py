@@ -20,7 +20,7 @@ def lib():
 def _declared():
     txt = open(os.path.join(ROOT, "include", "biolog.h")).read()
     txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
-    return sorted(set(re.findall(r"\b(bl_[a-z_]+)\s*\(", txt)))
+    return sorted(set(re.findall(r"\b(bl_[a-z0-9_]+)\s*\(", txt)))
 
 
 def test_exports_every_declared_symbol(lib):
