@@ -130,6 +130,7 @@ typedef struct bl_state {
 } bl_state;
 
 typedef struct bl_handle bl_handle;
+typedef struct bl_mlp bl_mlp;   /* learned move ranker, see bl_mlp_create */
 
 /* Bytes of device workspace bl_plan_init_batch needs for these instances and
    parameters (to pass a caller-owned buffer in bl_params.workspace). */
@@ -224,7 +225,6 @@ int bl_argmin_noalloc(bl_handle *h, int32_t inst, int32_t use_best, uint32_t ite
    weights are FP32; training minimises the mean squared error with Adam. All
    pointers named d_* are device memory owned by the caller; calls are
    asynchronous on the MLP's stream unless they return host values. */
-typedef struct bl_mlp bl_mlp;
 
 /* Create an MLP with He-uniform initial weights drawn from `seed`. in_dim in
    [1, 256], hidden a multiple of 16 in [16, 256], max_batch the largest M of
@@ -261,6 +261,27 @@ const char *bl_mlp_last_error(const bl_mlp *m);
    tensor cores gave up. */
 int bl_gemm_bf16(const uint16_t *d_a, const uint16_t *d_b, const float *d_bias, float *d_cf, uint16_t *d_cb, int32_t M,
                  int32_t N, int32_t K, int32_t relu, uint32_t *d_err, void *cuda_stream);
+
+/* Features of candidates i0..i0+n-1 of iteration `iter` (base x* if use_best
+   = 1, x_old if 0; use_best = -1 with iter = 0xFFFFFFFF takes the state's
+   current iteration and Eq. 5 choice): d_feat receives n x 64 BF16 values per
+   candidate (the move's kind, the distances around its removal and insertion
+   slots and the resulting HU-route change, field-to-BP distances, supply,
+   area, demand slack, completion-time slack of the tours involved, positions,
+   coordinates), normalised per instance. *d_base_cost (may be NULL) receives
+   the base plan's cost. Asynchronous on the handle's stream. */
+int bl_features(bl_handle *h, int32_t inst, int32_t use_best, uint32_t iter, int32_t i0, int32_t n, uint16_t *d_feat,
+                float *d_base_cost);
+
+/* Algorithm 1 with learned proposals, n_iters times (single-instance handle):
+   per iteration the first `pool` Philox candidates are featurised and ranked
+   by `mlp` (predicted cost change, lower is better); the n_keep best plus a
+   fraction rand_frac of the others, drawn uniformly, are scored exactly by the
+   same kernel as bl_search_step, which takes the argmin and updates the state.
+   Every accepted plan is thus judged by the exact score. pool <= n_cand of the
+   handle; the MLP must have been created on the handle's stream with
+   max_batch >= pool. The first call allocates the pool buffers. */
+int bl_search_step_learned(bl_handle *h, bl_mlp *mlp, int32_t n_iters, int32_t pool, int32_t n_keep, float rand_frac);
 
 /* Kernel configuration in use: threads per block, grid blocks, candidates
    per work item, and the number of kernels one iteration launches. */

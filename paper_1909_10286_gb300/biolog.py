@@ -26,7 +26,7 @@ EXPORTS = ("bl_workspace_bytes", "bl_plan_init", "bl_plan_init_batch", "bl_searc
            "bl_get_state", "bl_set_state", "bl_get_log", "bl_score_candidates", "bl_decode_candidates",
            "bl_get_config", "bl_plan_free", "bl_last_error", "bl_global_error", "bl_argmin_noalloc",
            "bl_mlp_create", "bl_mlp_forward", "bl_mlp_grads", "bl_mlp_train_step", "bl_mlp_get", "bl_mlp_set",
-           "bl_mlp_free", "bl_mlp_last_error", "bl_gemm_bf16")
+           "bl_mlp_free", "bl_mlp_last_error", "bl_gemm_bf16", "bl_features", "bl_search_step_learned")
 
 
 class BiologError(RuntimeError):
@@ -90,6 +90,8 @@ def load(path: str | None = None):
             L.bl_get_config.argtypes = [vp, vp, vp, vp, vp]
             L.bl_argmin_noalloc.argtypes = [vp, C.c_int32, C.c_int32, C.c_uint32, C.c_float, C.c_int32, C.c_int32,
                                             vp, vp]
+            L.bl_features.argtypes = [vp, C.c_int32, C.c_int32, C.c_uint32, C.c_int32, C.c_int32, vp, vp]
+            L.bl_search_step_learned.argtypes = [vp, vp, C.c_int32, C.c_int32, C.c_int32, C.c_float]
             L.bl_plan_free.argtypes = [vp]
             L.bl_last_error.argtypes = [vp]
             L.bl_last_error.restype = C.c_char_p
@@ -238,6 +240,21 @@ class Search:
         (key_ptr: 8 bytes, tmax_ptr: 4 bytes); the library allocates nothing for it."""
         _check(load().bl_argmin_noalloc(self.h, int(inst), int(use_best), int(iter_), float(tmax_star), int(i0),
                                         int(n), C.c_void_p(key_ptr), C.c_void_p(tmax_ptr)), self.h)
+
+    def features(self, use_best: int, iter_: int, i0: int, n: int, feat, base_cost=None, inst: int = 0):
+        """bl_features into a caller-owned torch bf16 tensor feat [>= n x 64] (and base_cost [1] float32)."""
+        _check(load().bl_features(self.h, int(inst), int(use_best), int(iter_), int(i0), int(n),
+                                  C.c_void_p(feat.data_ptr()),
+                                  None if base_cost is None else C.c_void_p(base_cost.data_ptr())), self.h)
+
+    def search_step_learned(self, mlp, n_iters: int, pool: int, n_keep: int, rand_frac: float = 0.1):
+        """bl_search_step_learned with a paper_1909_10286_gb300.mlp.MLP created on this handle's stream."""
+        _check(load().bl_search_step_learned(self.h, mlp.h, int(n_iters), int(pool), int(n_keep), float(rand_frac)),
+               self.h)
+
+    @property
+    def stream(self):
+        return self._stream
 
     def config(self) -> dict:
         v = [C.c_int32() for _ in range(4)]

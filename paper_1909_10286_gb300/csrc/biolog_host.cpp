@@ -17,6 +17,10 @@
 
 using namespace biolog;
 
+namespace biolog {
+cudaStream_t mlp_stream_of(const bl_mlp *m);   // biolog_mlp_host.cpp
+}
+
 namespace {
 
 thread_local std::string g_error;
@@ -341,6 +345,13 @@ struct bl_handle {
     int log_cap = 4096;
     cudaGraphExec_t graph = nullptr;
     InstState staged_state{};
+    // learned proposal mode: pool features, predictions, selected list (allocated on first use)
+    int32_t learned_pool = 0;
+    uint32_t learned_iters = 0;   // salt of the random fallback
+    uint16_t *l_feat = nullptr;
+    float *l_y = nullptr, *l_thresh = nullptr;
+    uint32_t *l_list = nullptr;
+    int32_t *l_count = nullptr;
     std::string err;
     bool failed = false;
     template <class T>
@@ -624,6 +635,19 @@ int init_common(const bl_instance *insts, int32_t n_inst, const bl_params *param
         M.dq_inv = std::ldexp(1.0f, -hi.dq_exp);
         M.dq_scale = std::ldexp(1.0f, hi.dq_exp);
         M.aq_scale = std::ldexp(1.0f, hi.areaq.exp);
+        {
+            double dsum = 0.0, ssum = 0.0, asum = 0.0;
+            for (int f = 0; f < hi.F; ++f) {
+                for (int b = 0; b < hi.B; ++b) dsum += hi.D64[(size_t)(1 + hi.B + f) * hi.N + 1 + b];
+                ssum += hi.supply[(size_t)f];
+                asum += hi.area[(size_t)f];
+            }
+            const double l0 = dsum / ((double)hi.F * hi.B);
+            M.inv_l0 = (float)(l0 > 0 ? 1.0 / l0 : 1.0);
+            M.inv_mean_supply = (float)(hi.F / ssum);
+            M.inv_mean_area = (float)(hi.F / asum);
+            M.mean_fields_per_bp = (float)hi.F / (float)hi.B;
+        }
         M.L = hi.L;
         M.blob = h->at<unsigned char>(h->ws.blob[(size_t)i]);
         M.xold = h->at<int16_t>(h->ws.xold[(size_t)i]);
@@ -897,6 +921,55 @@ int bl_argmin_noalloc(bl_handle *h, int32_t inst, int32_t use_best, uint32_t ite
     return BL_OK;
 }
 
+int bl_features(bl_handle *h, int32_t inst, int32_t use_best, uint32_t iter, int32_t i0, int32_t n, uint16_t *d_feat,
+                float *d_base_cost)
+{
+    if (!h || inst < 0 || inst >= h->n_inst || i0 < 0 || n < 1 || !d_feat) return BL_EINVAL;
+    if (h->failed) return BL_ESTATE;
+    CK(h, launch_features(h->cfg, h->at<InstMeta>(h->ws.meta), inst, use_best, iter, i0, n, h->sp, d_feat, d_base_cost,
+                          h->stream));
+    return BL_OK;
+}
+
+int bl_search_step_learned(bl_handle *h, bl_mlp *mlp, int32_t n_iters, int32_t pool, int32_t n_keep, float rand_frac)
+{
+    if (!h || !mlp || n_iters < 0 || pool < 1 || n_keep < 1 || n_keep > pool || !(rand_frac >= 0.f && rand_frac <= 1.f))
+        return BL_EINVAL;
+    if (h->failed) return BL_ESTATE;
+    if (h->n_inst != 1) { h->err = "learned proposals: one instance per handle"; return BL_EINVAL; }
+    if (mlp_stream_of(mlp) != h->stream) {
+        h->err = "learned proposals: create the MLP on the search handle's stream";
+        return BL_EINVAL;
+    }
+    if (pool > h->meta[0].n_cand) {
+        h->err = "learned proposals: pool must not exceed the handle's n_cand (the work decomposition)";
+        return BL_EINVAL;
+    }
+    if (h->learned_pool < pool) {
+        if (h->l_feat) { cudaFree(h->l_feat); cudaFree(h->l_y); cudaFree(h->l_list); cudaFree(h->l_count); }
+        CK(h, cudaMalloc((void **)&h->l_feat, (size_t)pool * NFEAT * 2));
+        CK(h, cudaMalloc((void **)&h->l_y, (size_t)pool * 4));
+        CK(h, cudaMalloc((void **)&h->l_list, (size_t)pool * 4));
+        CK(h, cudaMalloc((void **)&h->l_count, 16));
+        h->l_thresh = reinterpret_cast<float *>(h->l_count + 2);
+        h->learned_pool = pool;
+    }
+    for (int it = 0; it < n_iters; ++it) {
+        // the iteration's base (Eq. 5) and counter are read on the device by every kernel
+        CK(h, launch_features(h->cfg, h->at<InstMeta>(h->ws.meta), 0, -1, 0xffffffffu, 0, pool, h->sp, h->l_feat,
+                              nullptr, h->stream));
+        int rc = bl_mlp_forward(mlp, h->l_feat, pool, h->l_y);
+        if (rc != BL_OK) { h->err = "learned proposals: MLP forward failed"; return rc; }
+        CK(h, launch_select(h->l_y, pool, n_keep, rand_frac, 0x9E37u + h->learned_iters++, h->l_list, h->l_count,
+                            h->l_thresh, h->stream));
+        CK(h, launch_search_iteration(h->cfg, h->at<InstMeta>(h->ws.meta), h->at<WorkItem>(h->ws.work),
+                                      (int32_t)h->work.size(), h->sp, h->at<unsigned long long>(h->ws.slot_key),
+                                      h->at<float>(h->ws.slot_tmax), h->at<int32_t>(h->ws.slot_base), h->stream,
+                                      h->l_list, h->l_count));
+    }
+    return BL_OK;
+}
+
 int bl_best_plan(bl_handle *h, int32_t inst, bl_plan *out)
 {
     if (!h || !out || inst < 0 || inst >= h->n_inst) return BL_EINVAL;
@@ -965,6 +1038,10 @@ int bl_plan_free(bl_handle *h)
     if (h->graph) cudaGraphExecDestroy(h->graph);
     if (h->capture_stream) cudaStreamDestroy(h->capture_stream);
     if (h->own_ws && h->base) cudaFree(h->base);
+    if (h->l_feat) cudaFree(h->l_feat);
+    if (h->l_y) cudaFree(h->l_y);
+    if (h->l_list) cudaFree(h->l_list);
+    if (h->l_count) cudaFree(h->l_count);
     delete h;
     return BL_OK;
 }

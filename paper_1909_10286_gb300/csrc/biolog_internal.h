@@ -54,6 +54,10 @@ struct InstMeta {
     float dq_inv;              // distances -> fixed point: round(d * dq_inv)
     float dq_scale;            // and back: 2^k
     float aq_scale;            // fixed-point areas -> ha
+    float inv_l0;              // 1 / mean field-to-BP distance (feature scale)
+    float inv_mean_supply;     // 1 / mean field supply
+    float inv_mean_area;       // 1 / mean field area
+    float mean_fields_per_bp;  // F / B
     BlobLayout L;
     const unsigned char *blob; // device: this instance's table blob
     int16_t *xold;             // device: plan encodings (plan_len int16 each)
@@ -112,7 +116,14 @@ struct LaunchCfg {
 // Launch wrappers (biolog_kernels.cu).
 cudaError_t launch_search_iteration(const LaunchCfg &cfg, const InstMeta *d_meta, const WorkItem *d_work,
                                     int32_t n_work, SearchParams prm, unsigned long long *slot_key,
-                                    float *slot_tmax, const int32_t *slot_base, cudaStream_t s);
+                                    float *slot_tmax, const int32_t *slot_base, cudaStream_t s,
+                                    const uint32_t *cand_list = nullptr, const int32_t *cand_count = nullptr);
+constexpr int NFEAT = 64;   // features per candidate move
+cudaError_t launch_features(const LaunchCfg &cfg, const InstMeta *d_meta, int32_t inst, int32_t use_best,
+                            uint32_t iter, int32_t i0, int32_t n, SearchParams prm, uint16_t *d_feat,
+                            float *d_base_cost, cudaStream_t s);
+cudaError_t launch_select(const float *d_y, int32_t P, int32_t n_keep, float rand_frac, uint32_t salt,
+                          uint32_t *d_list, int32_t *d_count, float *d_thresh, cudaStream_t s);
 cudaError_t launch_score_dump(const LaunchCfg &cfg, const InstMeta *d_meta, int32_t inst, int32_t use_best,
                               uint32_t iter, float tmax_star, int32_t i0, int32_t n, int32_t identity,
                               SearchParams prm, float *d_cost, float *d_tmax, int16_t *d_moves, int16_t *d_nhu,

@@ -25,6 +25,7 @@
 // Per-tour state of a candidate lives in registers (up to 4 tours) or in
 // shared memory, one column per thread (more tours).
 #include <cstdint>
+#include <cuda_bf16.h>
 #include <mutex>
 #include <type_traits>
 #include <cuda_runtime.h>
@@ -522,7 +523,7 @@ struct TourState {
         unsigned long long *w = (unsigned long long *)((M *)((S *)((int *)base + (size_t)(NF32 + 1) * C) + 2 * C) + 2 * C) + tid;
         S1.p = w; Sh.p = w + C;
     }
-    static constexpr size_t bytes()
+    __host__ __device__ static constexpr size_t bytes()
     {
         constexpr size_t C = (size_t)MAXT * NT;
         return (NF32 + 1) * C * 4 + 2 * C * sizeof(S) + 2 * C * sizeof(M) + 2 * C * 8;
@@ -896,6 +897,8 @@ struct BlockShared {
     int32_t last;
     int32_t use_best;
     uint32_t iter;
+    float base_cost;
+    float base_tc[16];
     unsigned long long red[32];
     float redt[32];
 };
@@ -1036,14 +1039,22 @@ __device__ bool stage_instance(const InstMeta &M, BlockShared &bs, unsigned char
     if (tid == 0) {
         c.nbad = bs.nbad;
         for (int g = 0; g < T; ++g) { kf_base[g] = 0.f; sh_base[g] = 0; }
+        bs.base_cost = __int_as_float(0x7f800000);
+        for (int g = 0; g < T && g < 16; ++g) bs.base_tc[g] = 0.f;
         if (bs.nbad == 0) {
             const MoveRec idm = {4, 0, 0, 0};
-            score_candidate<SH, false>(c, p, idm, __int_as_float(0x7f800000), smem + sp.off_tour, tid, nullptr,
-                                       nullptr, nullptr, nullptr, nullptr, nullptr, nullptr);
+            const ScoreOut r = score_candidate<SH, false>(c, p, idm, __int_as_float(0x7f800000), smem + sp.off_tour,
+                                                          tid, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr,
+                                                          nullptr);
             TourState<SH> ts;
             ts.bind(smem + sp.off_tour, tid);
             for (int g = 0; g < T; ++g)
-                if (c.tour_cnt[g] > 0) { kf_base[g] = ts.KF.get(g); sh_base[g] = (long long)ts.Sh.get(g); }
+                if (c.tour_cnt[g] > 0) {
+                    kf_base[g] = ts.KF.get(g);
+                    sh_base[g] = (long long)ts.Sh.get(g);
+                    if (g < 16) bs.base_tc[g] = ts.Tc.get(g);
+                }
+            bs.base_cost = r.cost;
         }
     }
     __syncthreads();
@@ -1085,13 +1096,17 @@ __global__ void __launch_bounds__(SH::NT, SH::MINB) search_iteration_kernel(cons
                                                                   SearchParams prm, SmemPlan sp,
                                                                   unsigned long long *__restrict__ slot_key,
                                                                   float *__restrict__ slot_tmax,
-                                                                  const int32_t *__restrict__ slot_base)
+                                                                  const int32_t *__restrict__ slot_base,
+                                                                  const uint32_t *__restrict__ cand_list,
+                                                                  const int32_t *__restrict__ cand_count)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ BlockShared bs;
     const int tid = threadIdx.x;
     const int lane = tid & 31, warp = tid >> 5;
     constexpr int NT = SH::NT;
+    // list mode (learned proposals): positions index a list of candidate numbers
+    const int list_n = cand_list ? *cand_count : 0;
     if (tid == 0) {
         mbar_init(&bs.mbar, 1);
         fence_mbar_init();
@@ -1113,18 +1128,23 @@ __global__ void __launch_bounds__(SH::NT, SH::MINB) search_iteration_kernel(cons
         }
         const float tmax_star = M.state->tmaxstar;
         const uint32_t iter = bs.iter;
-        const int c0 = wi.tile_idx * M.tile;
-        const int c1 = min(c0 + M.tile, M.n_cand);
+        // list mode: the kept candidates are dealt evenly over the instance's work items
+        // (a multiple of 32 each), whatever the tile the full pool was planned with
+        const int tl = cand_list ? max(32, ((min(M.n_cand, list_n) + M.n_tiles - 1) / M.n_tiles + 31) & ~31) : M.tile;
+        const int c0 = wi.tile_idx * tl;
+        const int c1 = min(c0 + tl, cand_list ? min(M.n_cand, list_n) : M.n_cand);
         unsigned long long best = ~0ull;
         float best_t = 0.f;
         // each warp: draw 32 moves at a time, queue the feasible ones, score 32 queued at a time
         int qhead = 0, qcount = 0;   // warp-uniform ring-buffer state
         for (int base = c0 + warp * 32; base < c1 || qcount > 0; base += NT) {
+            // (c1 may be below c0 in list mode: then the work item only reports an empty slot)
             if (base < c1) {
-                const int i = base + lane;
+                const int pos = base + lane;
+                const int i = (cand_list && pos < c1) ? (int)cand_list[pos] : pos;
                 bool feas = false;
                 MoveRec m = {4, 0, 0, 0};
-                if (i < c1) {
+                if (pos < c1) {
                     m = draw_move(c, prm, (uint32_t)i, iter, M.inst_idx);
                     feas = demand_ok(c, m);
                     if (!feas) {
@@ -1263,7 +1283,7 @@ __global__ void __launch_bounds__(SH::NT) score_dump_kernel(const InstMeta *__re
     const int T = M.T;
     for (int k = blockIdx.x * nt + tid; k < n; k += gridDim.x * nt) {
         const int i = i0 + k;
-        MoveRec m = identity ? MoveRec{4, 0, 0, 0} : draw_move(c, prm, (uint32_t)i, iter, M.inst_idx);
+        MoveRec m = identity ? MoveRec{4, 0, 0, 0} : draw_move(c, prm, (uint32_t)i, bs.iter, M.inst_idx);
         if (moves) {
             moves[k * 4] = (int16_t)m.kind; moves[k * 4 + 1] = (int16_t)m.v;
             moves[k * 4 + 2] = (int16_t)m.a; moves[k * 4 + 3] = (int16_t)m.b;
@@ -1313,8 +1333,218 @@ __global__ void __launch_bounds__(SH::NT) decode_kernel(const InstMeta *__restri
     if (!stage_instance<SH>(M, bs, smem, sp, prm, use_best, iter, c)) return;
     const int rowlen = 2 * M.B + M.T + M.F;
     for (int k = blockIdx.x * nt + tid; k < n; k += gridDim.x * nt) {
-        const MoveRec m = draw_move(c, prm, (uint32_t)idx[k], iter, M.inst_idx);
+        const MoveRec m = draw_move(c, prm, (uint32_t)idx[k], bs.iter, M.inst_idx);
         write_plan(c, m, plans + (size_t)k * rowlen);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Features of candidate moves for the learned ranking (an extension: the
+// paper draws moves uniformly). One row of NFEAT BF16 values per candidate,
+// normalised per instance (distances by the mean field-to-BP distance, times
+// by Tmax*, supplies and areas by their means).
+// ---------------------------------------------------------------------------
+template <class SH>
+__global__ void __launch_bounds__(SH::NT) features_kernel(const InstMeta *__restrict__ meta, int32_t inst,
+                                                          int32_t use_best, uint32_t iter, int32_t i0, int32_t n,
+                                                          SearchParams prm, SmemPlan sp, __nv_bfloat16 *__restrict__ feat,
+                                                          float *__restrict__ base_cost)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ BlockShared bs;
+    const int tid = threadIdx.x, nt = blockDim.x;
+    if (tid == 0) {
+        mbar_init(&bs.mbar, 1);
+        fence_mbar_init();
+        bs.phase = 0;
+    }
+    __syncthreads();
+    const InstMeta &M = meta[inst];
+    Ctx c;
+    if (!stage_instance<SH>(M, bs, smem, sp, prm, use_best, iter, c)) return;
+    if (blockIdx.x == 0 && tid == 0 && base_cost) *base_cost = bs.base_cost;
+    const uint32_t it = bs.iter;   // resolved from the state when the caller passed 0xffffffff
+    const float tstar = M.state->tmaxstar;
+    const float inv_t = (tstar > 0.f && isfinite(tstar)) ? 1.f / tstar : 0.f;
+    const float L = c.dq_scale * M.inv_l0;   // fixed-point distance -> normalised distance
+    auto dn = [&](int a, int b) -> float { return (float)c.dq(a, b) * L; };
+    auto xy_of = [&](int node, float *out) {   // node position relative to the HQ, from distances to two references
+        out[0] = dn(0, node);
+        out[1] = dn(1, node);   // distance to BP 0 as the second coordinate
+    };
+    for (int k = blockIdx.x * nt + tid; k < n; k += gridDim.x * nt) {
+        const int i = i0 + k;
+        const MoveRec m = draw_move(c, prm, (uint32_t)i, it, M.inst_idx);
+        float f[NFEAT];
+#pragma unroll
+        for (int j = 0; j < NFEAT; ++j) f[j] = 0.f;
+        f[0] = m.kind == 0; f[1] = m.kind == 1; f[2] = m.kind >= 2;
+        View x;
+        x.set(c, m);
+        int tgs = -1, tgd = -1;   // source and destination tour of a reinsert
+        long long aqm = 0;        // area it moves (fixed point)
+        if (m.kind == 0) {
+            const int v = m.v, vn = 1 + c.B + v, bsrc = x.sg, bdst = x.dg, ps = x.sp, pd = x.dp;
+            const int gs = c.bp_tour[bsrc], gd = c.bp_tour[bdst];
+            tgs = gs; tgd = gd; aqm = c.areaq[v];
+            const int st = c.bp_start[bsrc], cnt = c.bp_cnt[bsrc];
+            // neighbours of v in its tour's field sequence (HQ at the ends)
+            int p = 0, q = 0;
+            if (ps > 0) p = 1 + c.B + c.field_order[st + ps - 1];
+            else if (c.bp_pos[bsrc] > 0) p = c.blast[c.bp_order[c.tour_start[gs] + c.bp_pos[bsrc] - 1]];
+            if (ps < cnt - 1) q = 1 + c.B + c.field_order[st + ps + 1];
+            else if (c.bp_pos[bsrc] < c.tour_cnt[gs] - 1) q = c.bfirst[c.bp_order[c.tour_start[gs] + c.bp_pos[bsrc] + 1]];
+            if (p < 0) p = 0;
+            if (q < 0) q = 0;
+            // neighbours at the insertion slot (destination list after the removal)
+            const int dst = c.bp_start[bdst];
+            const int len = c.bp_cnt[bdst] - (bdst == bsrc ? 1 : 0);
+            const bool same = (bdst == bsrc);
+            int a = (c.bp_pos[bdst] > 0) ? c.blast[c.bp_order[c.tour_start[gd] + c.bp_pos[bdst] - 1]] : 0;
+            int cc = (c.bp_pos[bdst] < c.tour_cnt[gd] - 1) ? c.bfirst[c.bp_order[c.tour_start[gd] + c.bp_pos[bdst] + 1]] : 0;
+            if (pd > 0) { const int j = pd - 1; a = 1 + c.B + c.field_order[dst + (same && j >= ps ? j + 1 : j)]; }
+            if (pd < len) { const int j = pd; cc = 1 + c.B + c.field_order[dst + (same && j >= ps ? j + 1 : j)]; }
+            if (a < 0) a = 0;
+            if (cc < 0) cc = 0;
+            f[3] = dn(p, vn); f[4] = dn(vn, q); f[5] = dn(p, q);
+            f[6] = dn(a, vn); f[7] = dn(vn, cc); f[8] = dn(a, cc);
+            f[9] = f[5] - f[3] - f[4];
+            f[10] = f[6] + f[7] - f[8];
+            f[11] = dn(vn, 1 + bsrc); f[12] = dn(vn, 1 + bdst); f[13] = f[12] - f[11];
+            f[14] = c.supply[v] * M.inv_mean_supply;
+            f[15] = c.area[v] * M.inv_mean_area;
+            const double ds = (double)c.demq[bsrc], dd = (double)c.demq[bdst];
+            f[16] = (float)(((double)c.base_supq[bsrc] - (same ? 0.0 : (double)c.supq[v]) - ds) / ds);
+            f[17] = (float)(((double)c.base_supq[bdst] + (same ? 0.0 : (double)c.supq[v]) - dd) / dd);
+            f[18] = same; f[19] = (gs == gd);
+            f[20] = gs < 16 ? (tstar - bs.base_tc[gs]) * inv_t : 0.f;
+            f[21] = gd < 16 ? (tstar - bs.base_tc[gd]) * inv_t : 0.f;
+            f[22] = (float)ps / (float)cnt;
+            f[23] = (float)pd / (float)(len + 1);
+            xy_of(vn, f + 24); xy_of(1 + bsrc, f + 26); xy_of(1 + bdst, f + 28);
+            f[30] = (float)cnt / M.mean_fields_per_bp;
+            f[31] = (float)(len + 1) / M.mean_fields_per_bp;
+            f[32] = f[9] + f[10];
+        } else if (m.kind == 1) {
+            const int b = m.v, gs = x.sg, gd = x.dg, qs = x.sp, qd = x.dp;
+            tgs = gs; tgd = gd; aqm = c.barea[b];
+            const int f1 = c.bfirst[b] >= 0 ? c.bfirst[b] : 0, fl = c.blast[b] >= 0 ? c.blast[b] : 0;
+            int p = 0, q = 0;
+            if (qs > 0) { const int t = c.blast[c.bp_order[c.tour_start[gs] + qs - 1]]; p = t >= 0 ? t : 0; }
+            if (qs < c.tour_cnt[gs] - 1) { const int t = c.bfirst[c.bp_order[c.tour_start[gs] + qs + 1]]; q = t >= 0 ? t : 0; }
+            // insertion slot in the destination tour after the removal
+            const int lenT = c.tour_cnt[gd] - (gd == gs ? 1 : 0);
+            auto bp_after = [&](int j) { return c.bp_order[c.tour_start[gd] + ((gd == gs && j >= qs) ? j + 1 : j)]; };
+            int a = 0, cc = 0;
+            if (qd > 0) { const int t = c.blast[bp_after(qd - 1)]; a = t >= 0 ? t : 0; }
+            if (qd < lenT) { const int t = c.bfirst[bp_after(qd)]; cc = t >= 0 ? t : 0; }
+            f[3] = dn(p, f1); f[4] = dn(fl, q); f[5] = dn(p, q);
+            f[6] = dn(a, f1); f[7] = dn(fl, cc); f[8] = dn(a, cc);
+            f[9] = f[5] - f[3] - f[4];
+            f[10] = f[6] + f[7] - f[8];
+            f[14] = (float)((double)c.base_supq[b] / (double)c.demq[b]);
+            f[15] = (float)((double)c.barea[b] * c.aq_scale) * M.inv_mean_area / fmaxf(M.mean_fields_per_bp, 1.f);
+            f[19] = (gs == gd);
+            f[20] = gs < 16 ? (tstar - bs.base_tc[gs]) * inv_t : 0.f;
+            f[21] = gd < 16 ? (tstar - bs.base_tc[gd]) * inv_t : 0.f;
+            f[22] = (float)qs / (float)c.tour_cnt[gs];
+            f[23] = (float)qd / (float)(lenT + 1);
+            xy_of(1 + b, f + 26);
+            f[30] = (float)c.bp_cnt[b] / M.mean_fields_per_bp;
+            f[32] = f[9] + f[10];
+        } else {
+            const int v = m.v, w = m.a;
+            const int vn = (m.kind == 2) ? 1 + c.B + v : 1 + v, wn = (m.kind == 2) ? 1 + c.B + w : 1 + w;
+            f[3] = dn(vn, wn);
+            xy_of(vn, f + 24); xy_of(wn, f + 26);
+        }
+        f[33] = demand_ok(c, m);   // Eq. 2, exact
+        if (tgs >= 0) {
+            // completion-time gate signals: share of each tour's area the move
+            // shifts, base completion times scaled by it, criticality, and the
+            // HU-route change relative to each tour's route
+            float tcmax = 0.f;
+            for (int g = 0; g < c.T; ++g) tcmax = fmaxf(tcmax, bs.base_tc[g]);
+            const bool other = (tgs != tgd);
+            const float ad = other && c.tA[tgd] > 0 ? (float)((double)aqm / (double)c.tA[tgd]) : 0.f;
+            const float as = other && c.tA[tgs] > 0 ? (float)((double)aqm / (double)c.tA[tgs]) : 0.f;
+            f[34] = fminf(ad, 4.f);
+            f[35] = as;
+            f[36] = bs.base_tc[tgd] * inv_t * (1.f + f[34]) - 1.f;
+            f[37] = bs.base_tc[tgs] * inv_t * (1.f - f[35]) - 1.f;
+            f[38] = bs.base_tc[tgs] >= tcmax;
+            f[39] = bs.base_tc[tgd] >= tcmax;
+            const float rl = 1.f / L;
+            f[40] = c.tLHU[tgd] > 0 ? fminf(f[10] * rl / (float)c.tLHU[tgd], 4.f) : 0.f;
+            f[41] = c.tLHU[tgs] > 0 ? fmaxf(f[9] * rl / (float)c.tLHU[tgs], -4.f) : 0.f;
+            f[42] = tcmax * inv_t - 1.f;
+        }
+#pragma unroll
+        for (int j = 0; j < NFEAT; ++j) f[j] = isfinite(f[j]) ? fminf(fmaxf(f[j], -64.f), 64.f) : 0.f;
+        __nv_bfloat16 *row = feat + (size_t)k * NFEAT;
+#pragma unroll
+        for (int j = 0; j < NFEAT; j += 2) {
+            const __nv_bfloat162 pr = __floats2bfloat162_rn(f[j], f[j + 1]);
+            *reinterpret_cast<__nv_bfloat162 *>(row + j) = pr;
+        }
+    }
+}
+
+// Selection of the moves to score exactly: the n_keep best predicted
+// (threshold from a sorted sample of 4096 predictions) plus a uniform random
+// fraction of the rest as fallback.
+__global__ void select_threshold_kernel(const float *__restrict__ y, int32_t P, int32_t n_keep, float *__restrict__ thresh)
+{
+    __shared__ float sbuf[4096];
+    const int S = 4096;
+    for (int j = threadIdx.x; j < S; j += blockDim.x) {
+        const long long idx = (long long)j * P / S;
+        const float v = y[idx];
+        sbuf[j] = isfinite(v) ? v : __int_as_float(0x7f800000);
+    }
+    __syncthreads();
+    // bitonic sort of the sample
+    for (int k = 2; k <= S; k <<= 1)
+        for (int jj = k >> 1; jj > 0; jj >>= 1) {
+            for (int t = threadIdx.x; t < S; t += blockDim.x) {
+                const int o = t ^ jj;
+                if (o > t) {
+                    const bool up = ((t & k) == 0);
+                    const float a = sbuf[t], b = sbuf[o];
+                    if ((a > b) == up) { sbuf[t] = b; sbuf[o] = a; }
+                }
+            }
+            __syncthreads();
+        }
+    if (threadIdx.x == 0) {
+        long long r = (long long)n_keep * S / P;
+        if (r >= S) r = S - 1;
+        if (r < 0) r = 0;
+        *thresh = sbuf[r];
+    }
+}
+
+__global__ void select_compact_kernel(const float *__restrict__ y, int32_t P, const float *__restrict__ thresh,
+                                      float rand_frac, uint32_t salt, uint32_t *__restrict__ list,
+                                      int32_t *__restrict__ count)
+{
+    const float th = *thresh;
+    const uint32_t cut = (uint32_t)(rand_frac * 4294967295.0f);
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < P; i += gridDim.x * blockDim.x) {
+        bool keep = y[i] <= th;
+        if (!keep) {
+            uint32_t r[4] = {(uint32_t)i, salt, 0x5E1EC7u, 2u};
+            philox10(r, 0x243F6A88u, 0x85A308D3u);
+            keep = r[0] < cut;
+        }
+        const unsigned act = __activemask();
+        const unsigned ball = __ballot_sync(act, keep);
+        const int lane = threadIdx.x & 31;
+        const int leader = __ffs(act) - 1;
+        int base = 0;
+        if (lane == leader && ball) base = atomicAdd(count, __popc(ball));
+        base = __shfl_sync(act, base, leader);
+        if (keep) list[base + __popc(ball & ((1u << lane) - 1u))] = (uint32_t)i;
     }
 }
 
@@ -1369,7 +1599,7 @@ __global__ void __launch_bounds__(SH::NT) argmin_noalloc_kernel(const InstMeta *
             bool feas = false;
             MoveRec m = {4, 0, 0, 0};
             if (i < c1) {
-                m = draw_move(c, prm, (uint32_t)i, iter, M.inst_idx);
+                m = draw_move(c, prm, (uint32_t)i, bs.iter, M.inst_idx);
                 feas = demand_ok(c, m);
                 if (!feas) {
                     const unsigned long long k = make_key(__int_as_float(0x7f800000), (uint32_t)i);
@@ -1501,21 +1731,22 @@ cudaError_t configure_kernels(int32_t shape, size_t smem)
 
 cudaError_t launch_search_iteration(const LaunchCfg &cfg, const InstMeta *d_meta, const WorkItem *d_work,
                                     int32_t n_work, SearchParams prm, unsigned long long *slot_key, float *slot_tmax,
-                                    const int32_t *slot_base, cudaStream_t s)
+                                    const int32_t *slot_base, cudaStream_t s, const uint32_t *cand_list,
+                                    const int32_t *cand_count)
 {
     const SmemPlan sp = plan_for(cfg);
     switch (cfg.shape) {
     case SHAPE_T4_S64_DSMEM:
-        search_iteration_kernel<ShapeA><<<cfg.grid, ShapeA::NT, sp.total, s>>>(d_meta, d_work, n_work, prm, sp,
-                                                                                slot_key, slot_tmax, slot_base);
+        search_iteration_kernel<ShapeA><<<cfg.grid, ShapeA::NT, sp.total, s>>>(
+            d_meta, d_work, n_work, prm, sp, slot_key, slot_tmax, slot_base, cand_list, cand_count);
         break;
     case SHAPE_T8_S64_DSMEM:
-        search_iteration_kernel<ShapeB><<<cfg.grid, ShapeB::NT, sp.total, s>>>(d_meta, d_work, n_work, prm, sp,
-                                                                                slot_key, slot_tmax, slot_base);
+        search_iteration_kernel<ShapeB><<<cfg.grid, ShapeB::NT, sp.total, s>>>(
+            d_meta, d_work, n_work, prm, sp, slot_key, slot_tmax, slot_base, cand_list, cand_count);
         break;
     default:
-        search_iteration_kernel<ShapeC><<<cfg.grid, ShapeC::NT, sp.total, s>>>(d_meta, d_work, n_work, prm, sp,
-                                                                                slot_key, slot_tmax, slot_base);
+        search_iteration_kernel<ShapeC><<<cfg.grid, ShapeC::NT, sp.total, s>>>(
+            d_meta, d_work, n_work, prm, sp, slot_key, slot_tmax, slot_base, cand_list, cand_count);
     }
     return cudaGetLastError();
 }
@@ -1576,6 +1807,47 @@ cudaError_t launch_argmin_noalloc(const LaunchCfg &cfg, const InstMeta *d_meta, 
     }
 #undef NA_ARGS
     if (e != cudaSuccess) return e;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_features(const LaunchCfg &cfg, const InstMeta *d_meta, int32_t inst, int32_t use_best,
+                            uint32_t iter, int32_t i0, int32_t n, SearchParams prm, uint16_t *d_feat,
+                            float *d_base_cost, cudaStream_t s)
+{
+    const SmemPlan sp = plan_for(cfg);
+    const int nt = threads_of(cfg.shape);
+    int grid = (n + nt - 1) / nt;
+    if (grid > cfg.grid) grid = cfg.grid;
+    if (grid < 1) grid = 1;
+    __nv_bfloat16 *f = reinterpret_cast<__nv_bfloat16 *>(d_feat);
+    cudaError_t e;
+    switch (cfg.shape) {
+    case SHAPE_T4_S64_DSMEM:
+        e = cudaFuncSetAttribute(features_kernel<ShapeA>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sp.total);
+        if (e == cudaSuccess)
+            features_kernel<ShapeA><<<grid, nt, sp.total, s>>>(d_meta, inst, use_best, iter, i0, n, prm, sp, f, d_base_cost);
+        break;
+    case SHAPE_T8_S64_DSMEM:
+        e = cudaFuncSetAttribute(features_kernel<ShapeB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sp.total);
+        if (e == cudaSuccess)
+            features_kernel<ShapeB><<<grid, nt, sp.total, s>>>(d_meta, inst, use_best, iter, i0, n, prm, sp, f, d_base_cost);
+        break;
+    default:
+        e = cudaFuncSetAttribute(features_kernel<ShapeC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sp.total);
+        if (e == cudaSuccess)
+            features_kernel<ShapeC><<<grid, nt, sp.total, s>>>(d_meta, inst, use_best, iter, i0, n, prm, sp, f, d_base_cost);
+    }
+    if (e != cudaSuccess) return e;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_select(const float *d_y, int32_t P, int32_t n_keep, float rand_frac, uint32_t salt,
+                          uint32_t *d_list, int32_t *d_count, float *d_thresh, cudaStream_t s)
+{
+    cudaError_t e = cudaMemsetAsync(d_count, 0, sizeof(int32_t), s);
+    if (e != cudaSuccess) return e;
+    select_threshold_kernel<<<1, 1024, 0, s>>>(d_y, P, n_keep, d_thresh);
+    select_compact_kernel<<<592, 256, 0, s>>>(d_y, P, d_thresh, rand_frac, salt, d_list, d_count);
     return cudaGetLastError();
 }
 

@@ -32,6 +32,10 @@ namespace {
 thread_local std::string g_mlp_error;
 }
 
+namespace biolog {
+cudaStream_t mlp_stream_of(const bl_mlp *m);
+}
+
 struct bl_mlp {
     int in = 0, H = 0, max_batch = 0;
     cudaStream_t stream = nullptr;
@@ -141,6 +145,8 @@ int backward(bl_mlp *m, const uint16_t *x, int M)
 }
 
 }  // namespace
+
+cudaStream_t biolog::mlp_stream_of(const bl_mlp *m) { return m->stream; }
 
 extern "C" {
 

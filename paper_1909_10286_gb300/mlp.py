@@ -85,6 +85,12 @@ class MLP:
         arrs = [np.ascontiguousarray(a, dtype=np.float32) for a in arrs]
         _check(_lib().bl_mlp_set(self.h, *[_np(a) for a in arrs]), self.h)
 
+    def copy(self, stream=None, max_batch: int | None = None) -> "MLP":
+        """A network with the same weights (Adam state reset), e.g. on a search handle's stream."""
+        net = MLP(self.in_dim, self.hidden, max_batch or self.max_batch, stream=stream)
+        net.set(self.get())
+        return net
+
     def forward(self, x, y=None):
         import torch
 
