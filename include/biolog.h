@@ -231,7 +231,13 @@ int bl_argmin_noalloc(bl_handle *h, int32_t inst, int32_t use_best, uint32_t ite
    later calls. Owns its device memory. */
 int bl_mlp_create(int32_t in_dim, int32_t hidden, int32_t max_batch, uint64_t seed, void *cuda_stream, bl_mlp **out);
 
-/* y[M] = MLP(x[M x in_dim]), x BF16 row-major. */
+/* y[M] = MLP(x[M x in_dim]), x BF16 row-major, asynchronously on the MLP's
+   stream. When hidden is a multiple of 32 the three layers and the head run
+   as one fused tensor-core kernel (activations stay on chip, rounded to BF16
+   between layers like the layer-by-layer pass) and M is not bounded by
+   max_batch; otherwise M <= max_batch. A bounded wait that gave up inside a
+   kernel sets the MLP's error flag, reported as BL_ETIMEOUT by the next
+   bl_mlp_grads / bl_mlp_train_step. */
 int bl_mlp_forward(bl_mlp *m, const uint16_t *d_x, int32_t M, float *d_y);
 
 /* Forward and backward pass of the loss mean_i (y_i - t_i)^2 without

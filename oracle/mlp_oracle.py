@@ -27,6 +27,17 @@ def forward(params, x):
     return y, (h1, h2, h3)
 
 
+def forward_bf16(params, x):
+    """forward() with every hidden activation rounded to bfloat16 after its
+    ReLU, as the tensor-core path stores them between layers (the products
+    and sums themselves stay exact in FP64)."""
+    w1, b1, w2, b2, w3, b3, w4, b4 = [np.asarray(p, dtype=np.float64) for p in params]
+    h1 = bf16(np.maximum(x @ w1.T + b1, 0.0))
+    h2 = bf16(np.maximum(h1 @ w2.T + b2, 0.0))
+    h3 = bf16(np.maximum(h2 @ w3.T + b3, 0.0))
+    return h3 @ w4 + b4[0], (h1, h2, h3)
+
+
 def grads(params, x, t):
     """Gradients of mean((y - t)^2) with respect to every parameter."""
     w1, b1, w2, b2, w3, b3, w4, b4 = [np.asarray(p, dtype=np.float64) for p in params]

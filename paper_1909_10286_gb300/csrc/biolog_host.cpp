@@ -436,11 +436,12 @@ void plan_work(bl_handle *h, int sms, int blocks_per_sm)
     long long total = (long long)n * h->prm.n_cand;
     int tile = h->prm.tile;
     if (tile <= 0) {
-        // about 4 work items per block over the whole batch, at least one candidate per thread
+        // about 4 work items per block over the whole batch, at least one candidate per
+        // thread; whole warps (not whole blocks), so a single instance fills every block
         long long per = (total + (long long)grid * 4 - 1) / ((long long)grid * 4);
         if (n == 1) per = (total + grid - 1) / grid;   // one balanced item per block
         per = std::max<long long>(per, threads);
-        per = (per + threads - 1) / threads * threads;
+        per = (per + 31) / 32 * 32;
         tile = (int)std::min<long long>(per, 1 << 30);
     }
     std::vector<int> order((size_t)n);

@@ -12,6 +12,7 @@
 // slab of 8x8 core matrices, (row group, k block) at offset (2 * rg + kb) * 128
 // bytes -- and one elected thread issues one tcgen05.mma per slice, committed
 // to an mbarrier that the CTA waits on with a wall-clock bound.
+#include <algorithm>
 #include <cstdint>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
@@ -74,6 +75,18 @@ __device__ __forceinline__ uint64_t smem_desc(const void *p, uint32_t lbo, uint3
 __host__ __device__ constexpr uint32_t instr_desc(int m, int n)
 {
     return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(m >> 4) << 24);
+}
+
+// eight FP32 values rounded to BF16 (round to nearest even), packed into 16 bytes
+__device__ __forceinline__ uint4 pack8_bf16(const float *x)
+{
+    uint32_t w[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const __nv_bfloat162 p = __floats2bfloat162_rn(x[2 * q], x[2 * q + 1]);
+        w[q] = *reinterpret_cast<const uint32_t *>(&p);
+    }
+    return make_uint4(w[0], w[1], w[2], w[3]);
 }
 
 // Copy a [rows x 64] BF16 chunk (row stride ld elements, starting at column k0)
@@ -166,6 +179,7 @@ gemm_bf16_tn_kernel(const __nv_bfloat16 *__restrict__ A, const __nv_bfloat16 *__
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     }
     if (ok) {
+        const bool vec_ok = (N % 8) == 0 && ((reinterpret_cast<uintptr_t>(Cb) | reinterpret_cast<uintptr_t>(Cf)) & 15) == 0;
         // epilogue: thread (warp w, lane l) owns row 32w + l of the tile
         const int row = m0 + warp * 32 + lane;
         const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16);
@@ -179,21 +193,345 @@ gemm_bf16_tn_kernel(const __nv_bfloat16 *__restrict__ A, const __nv_bfloat16 *__
                 : "r"(taddr + (uint32_t)c0));
             asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
             if (row < M) {
+                float x[16];
 #pragma unroll
                 for (int j = 0; j < 16; ++j) {
                     const int col = c0 + j;
-                    if (col >= N) break;
-                    float x = __uint_as_float(v[j]);
-                    if (bias) x += bias[col];
-                    if (relu) x = fmaxf(x, 0.f);
-                    if (Cf) Cf[(size_t)row * N + col] = x;
-                    if (Cb) Cb[(size_t)row * N + col] = __float2bfloat16(x);
+                    x[j] = __uint_as_float(v[j]);
+                    if (bias && col < N) x[j] += bias[col];
+                    if (relu) x[j] = fmaxf(x[j], 0.f);
+                }
+                // whole 16-column pieces of the row go out as 16-byte stores
+                if (vec_ok && c0 + 16 <= N) {
+                    if (Cb) {
+                        uint4 *d = reinterpret_cast<uint4 *>(Cb + (size_t)row * N + c0);
+                        d[0] = pack8_bf16(x);
+                        d[1] = pack8_bf16(x + 8);
+                    }
+                    if (Cf) {
+                        float4 *d = reinterpret_cast<float4 *>(Cf + (size_t)row * N + c0);
+#pragma unroll
+                        for (int q = 0; q < 4; ++q) d[q] = make_float4(x[4 * q], x[4 * q + 1], x[4 * q + 2], x[4 * q + 3]);
+                    }
+                } else {
+#pragma unroll
+                    for (int j = 0; j < 16; ++j) {
+                        const int col = c0 + j;
+                        if (col >= N) break;
+                        if (Cf) Cf[(size_t)row * N + col] = x[j];
+                        if (Cb) Cb[(size_t)row * N + col] = __float2bfloat16(x[j]);
+                    }
                 }
             }
         }
     } else {
         if (tid == 0) atomicExch(err, 1u);
         mbar_wait(&mbar, phase ^ 1u);   // give MMAs still in flight a second bounded chance before freeing TMEM
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS) : "memory");
+}
+
+// ---- fused inference: all three layers and the head per 128-row tile ------
+//
+// y = w4 . relu(W3 relu(W2 relu(W1 x + b1) + b2) + b3) + b4 for M rows, one
+// persistent CTA per SM looping over 128-row tiles. The accumulator of the
+// layer in flight is 128 TMEM lanes x H FP32 columns; the hidden activations
+// never leave shared memory: each layer's epilogue (bias, ReLU, BF16 rounding
+// -- the same rounding the layer-by-layer path stores) writes them straight
+// into the A-operand layout of the next layer. The weights of the three
+// layers are pre-packed (fused_pack_kernel) into K chunks of 64 in the
+// B-operand layout, so each chunk is one bulk copy into a ring of NBUF
+// shared buffers, loaded ahead while the tensor cores work on earlier chunks.
+//
+// Shared layouts (no swizzle, K-major, 8x8 core matrices of 16-byte rows):
+//   activations X (tile of the input) and Hs (hidden): core matrix (row group
+//   rg, k block kb) at kb * 2048 + rg * 128 bytes   -> LBO 2048, SBO 128
+//   weight chunk: core matrix (n group ng, k block kb) at kb * (H * 16) + ng * 128
+//                                                      -> LBO H * 16, SBO 128
+// Warp w (8 warps) reads TMEM lanes 32 (w % 4) .. +31 and the column half w / 4.
+constexpr int FTHREADS = 256;
+constexpr int FKC = 64;   // K per weight chunk
+
+__device__ __forceinline__ void mbar_expect_tx_bytes(uint64_t *bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar)
+{
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_u32(dst)),
+                 "l"(src), "r"(bytes), "r"(smem_u32(bar))
+                 : "memory");
+}
+
+__device__ __forceinline__ void tc_commit(uint64_t *bar)
+{
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+                 : "memory");
+}
+
+__device__ __forceinline__ void tc_mma(uint32_t tmem, uint64_t ad, uint64_t bd, uint32_t idesc, uint32_t acc)
+{
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem),
+        "l"(ad), "l"(bd), "r"(idesc), "r"(acc)
+        : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t *v)
+{
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+        : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]), "=r"(v[8]),
+          "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+// Pack W (layer l: [H x K_l] row-major BF16) into the chunked B-operand layout.
+// Chunk order: layer 1 chunks, layer 2 chunks, layer 3 chunks; K beyond K_l is zero.
+__global__ void fused_pack_kernel(const __nv_bfloat16 *__restrict__ w1, const __nv_bfloat16 *__restrict__ w2,
+                                  const __nv_bfloat16 *__restrict__ w3, int I, int H, int nch1, int nch2,
+                                  uint4 *__restrict__ out)
+{
+    const int segs_per_chunk = H * (FKC / 8);
+    const int total = (nch1 + 2 * nch2) * segs_per_chunk;
+    for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < total; s += gridDim.x * blockDim.x) {
+        const int ch = s / segs_per_chunk, r = s % segs_per_chunk;
+        const int kb = r / H, n = r % H;   // 16-byte segment = row n of core matrix (n / 8, kb)
+        const __nv_bfloat16 *w;
+        int K, c;
+        if (ch < nch1) { w = w1; K = I; c = ch; }
+        else if (ch < nch1 + nch2) { w = w2; K = H; c = ch - nch1; }
+        else { w = w3; K = H; c = ch - nch1 - nch2; }
+        __nv_bfloat16 e[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            const int k = c * FKC + kb * 8 + q;
+            e[q] = k < K ? w[(size_t)n * K + k] : __float2bfloat16(0.f);
+        }
+        // byte offset kb * H * 16 + (n / 8) * 128 + (n % 8) * 16 = (kb * H + n) * 16
+        out[(size_t)ch * segs_per_chunk + (size_t)kb * H + n] = *reinterpret_cast<const uint4 *>(e);
+    }
+}
+
+struct FusedSmem {
+    int xs, hs, wb, par, nbuf, total;
+};
+
+__host__ __device__ inline FusedSmem fused_smem(int I, int H, int nbuf)
+{
+    FusedSmem f;
+    const int nch1 = (I + FKC - 1) / FKC, nch2 = (H + FKC - 1) / FKC;
+    f.xs = 0;
+    f.hs = f.xs + nch1 * (FKC / 8) * 2048;
+    f.wb = f.hs + nch2 * (FKC / 8) * 2048;
+    f.par = f.wb + nbuf * H * FKC * 2;
+    f.nbuf = nbuf;
+    f.total = f.par + (4 * H + 2 * 128 + 4) * 4;
+    return f;
+}
+
+// Stage rows [r0, r0 + 128) of X [M x I] into the activation layout (zero rows >= M, k >= I).
+__device__ __forceinline__ void fused_stage_x(unsigned char *xs, const __nv_bfloat16 *__restrict__ X, int M, int I,
+                                              int nkb, int r0, int t0, int nthr)
+{
+    const bool vec = (I % 8) == 0 && (reinterpret_cast<uintptr_t>(X) & 15) == 0;
+    for (int s = t0; s < 128 * nkb; s += nthr) {
+        const int r = s & 127, kb = s >> 7;   // consecutive threads: consecutive rows, conflict-free stores
+        const int row = r0 + r, k = kb * 8;
+        uint4 v = make_uint4(0u, 0u, 0u, 0u);
+        if (row < M && k < I) {
+            if (vec) v = __ldg(reinterpret_cast<const uint4 *>(X + (size_t)row * I + k));
+            else {
+                __nv_bfloat16 e[8];
+#pragma unroll
+                for (int q = 0; q < 8; ++q) e[q] = (k + q < I) ? X[(size_t)row * I + k + q] : __float2bfloat16(0.f);
+                v = *reinterpret_cast<const uint4 *>(e);
+            }
+        }
+        *reinterpret_cast<uint4 *>(xs + kb * 2048 + (r >> 3) * 128 + (r & 7) * 16) = v;
+    }
+}
+
+__global__ void __launch_bounds__(FTHREADS, 1)
+fused_mlp_forward_kernel(const __nv_bfloat16 *__restrict__ X, int M, int I, int H, const uint4 *__restrict__ wpack,
+                         const float *__restrict__ b1, const float *__restrict__ b2, const float *__restrict__ b3,
+                         const float *__restrict__ w4, const float *__restrict__ b4, float *__restrict__ y, int nbuf,
+                         unsigned int *__restrict__ err)
+{
+    extern __shared__ __align__(1024) unsigned char smem[];
+    __shared__ uint64_t tma_bar[4], mma_bar[4], layer_bar, drain_bar;
+    __shared__ uint32_t tmem_base_sh;
+    __shared__ int fail_sh;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int nch1 = (I + FKC - 1) / FKC, nch2 = (H + FKC - 1) / FKC, cpt = nch1 + 2 * nch2;
+    const FusedSmem L = fused_smem(I, H, nbuf);
+    unsigned char *xs = smem + L.xs, *hs = smem + L.hs, *wb = smem + L.wb;
+    float *par = reinterpret_cast<float *>(smem + L.par);   // b1 | b2 | b3 | w4 | red[2][128] | b4
+    float *red = par + 4 * H;
+    const uint32_t chunk_bytes = (uint32_t)H * FKC * 2;
+    const int ntiles = (M + 127) / 128;
+    const int my_tiles = blockIdx.x < ntiles ? (ntiles - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
+    const long long total = (long long)my_tiles * cpt;   // weight chunks this CTA consumes
+
+    for (int i = tid; i < H; i += FTHREADS) {
+        par[i] = b1[i]; par[H + i] = b2[i]; par[2 * H + i] = b3[i]; par[3 * H + i] = w4[i];
+    }
+    if (tid == 0) red[256] = b4[0];
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base_sh)),
+                     "r"(TMEM_COLS)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    if (tid == 0) {
+        for (int b = 0; b < 4; ++b) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&tma_bar[b])) : "memory");
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&mma_bar[b])) : "memory");
+        }
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&layer_bar)) : "memory");
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&drain_bar)) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        fail_sh = 0;
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = tmem_base_sh;
+    const uint32_t idesc = instr_desc(128, H);
+
+    // producer state (thread 0): chunks are loaded nbuf ahead; each barrier's
+    // completions are waited on in order, so one parity bit per barrier suffices
+    long long loaded = 0;        // chunks whose bulk copy was issued
+    long long consumed = 0;      // chunks whose MMAs were issued
+    uint32_t tma_ph = 0, mma_ph = 0;   // bit b: parity of the next wait on buffer b
+    auto load_chunk = [&](long long j) {
+        const int b = (int)(j % nbuf);
+        mbar_expect_tx_bytes(&tma_bar[b], chunk_bytes);
+        bulk_g2s(wb + (size_t)b * chunk_bytes, wpack + (size_t)(j % cpt) * (chunk_bytes / 16), chunk_bytes,
+                 &tma_bar[b]);
+    };
+    // issue the MMAs of the next chunk; returns false if a bounded wait gave up
+    auto consume_chunk = [&]() -> bool {
+        const long long j = consumed;
+        const int b = (int)(j % nbuf);
+        if (!mbar_wait(&tma_bar[b], (tma_ph >> b) & 1u)) return false;
+        tma_ph ^= 1u << b;
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const int jj = (int)(j % cpt);
+        const int layer = jj < nch1 ? 0 : (jj < nch1 + nch2 ? 1 : 2);
+        const int c = layer == 0 ? jj : (layer == 1 ? jj - nch1 : jj - nch1 - nch2);
+        const int K = layer == 0 ? I : H;
+        const unsigned char *A = layer == 0 ? xs : hs;
+        const unsigned char *B = wb + (size_t)b * chunk_bytes;
+#pragma unroll
+        for (int s = 0; s < FKC / 16; ++s) {
+            const int k = c * FKC + s * 16;
+            if (k >= K) break;
+            const uint64_t ad = smem_desc(A + (size_t)(k / 8) * 2048, 2048, 128);
+            const uint64_t bd = smem_desc(B + (size_t)(2 * s) * H * 16, (uint32_t)H * 16, 128);
+            tc_mma(tmem, ad, bd, idesc, (c > 0 || s > 0) ? 1u : 0u);
+        }
+        tc_commit(&mma_bar[b]);
+        consumed = j + 1;
+        // the buffer of chunk j - 1 is free once its MMAs are done: load chunk j - 1 + nbuf into it
+        if (j >= 1 && loaded < total) {
+            const int pb = (int)((j - 1) % nbuf);
+            if (!mbar_wait(&mma_bar[pb], (mma_ph >> pb) & 1u)) return false;
+            mma_ph ^= 1u << pb;
+            load_chunk(loaded++);
+        }
+        return true;
+    };
+
+    if (tid == 0)
+        while (loaded < total && loaded < nbuf) load_chunk(loaded++);
+    const int q = warp & 3, half = warp >> 2;
+    const int row_in_tile = 32 * q + lane;
+    const int hcols = H / 2;
+    uint32_t layer_ph = 0;
+    bool ok = true;
+    if (my_tiles > 0) fused_stage_x(xs, X, M, I, nch1 * (FKC / 8), (int)blockIdx.x * 128, tid, FTHREADS);
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    __syncthreads();
+
+    for (int t = 0; t < my_tiles && ok; ++t) {
+        const int tile = (int)blockIdx.x + t * (int)gridDim.x;
+        const int next = tile + (int)gridDim.x;
+        for (int layer = 0; layer < 3 && ok; ++layer) {
+            const int nchunks = layer == 0 ? nch1 : nch2;
+            if (tid == 0) {
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                bool good = true;
+                for (int c = 0; c < nchunks && good; ++c) good = consume_chunk();
+                if (good) tc_commit(&layer_bar);
+                else fail_sh = 1;
+            } else if (layer == 1 && next < ntiles && tid >= 32) {
+                // layer 1's MMAs are done (its epilogue waited for them): X of the next tile can go in
+                fused_stage_x(xs, X, M, I, nch1 * (FKC / 8), next * 128, tid - 32, FTHREADS - 32);
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            }
+            __syncwarp();
+            const bool got = (volatile int &)fail_sh == 0 && mbar_wait(&layer_bar, layer_ph);
+            layer_ph ^= 1u;
+            ok = __syncthreads_and(got ? 1 : 0) != 0;
+            if (!ok) break;
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const uint32_t taddr = tmem + ((uint32_t)(32 * q) << 16);
+            const float *bias = par + layer * H;
+            if (layer < 2) {
+                for (int c0 = half * hcols; c0 < (half + 1) * hcols; c0 += 16) {
+                    uint32_t v[16];
+                    tmem_ld16(taddr + (uint32_t)c0, v);
+                    float x[16];
+#pragma unroll
+                    for (int e = 0; e < 16; ++e) x[e] = fmaxf(__uint_as_float(v[e]) + bias[c0 + e], 0.f);
+                    const int r = row_in_tile;
+                    unsigned char *dst = hs + (size_t)(c0 / 8) * 2048 + (r >> 3) * 128 + (r & 7) * 16;
+                    *reinterpret_cast<uint4 *>(dst) = pack8_bf16(x);
+                    *reinterpret_cast<uint4 *>(dst + 2048) = pack8_bf16(x + 8);
+                }
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            } else {
+                float acc = 0.f;
+                const float *wv = par + 3 * H;
+                for (int c0 = half * hcols; c0 < (half + 1) * hcols; c0 += 16) {
+                    uint32_t v[16];
+                    tmem_ld16(taddr + (uint32_t)c0, v);
+#pragma unroll
+                    for (int e = 0; e < 16; ++e) {
+                        const float h = __bfloat162float(__float2bfloat16(fmaxf(__uint_as_float(v[e]) + bias[c0 + e], 0.f)));
+                        acc = fmaf(h, wv[c0 + e], acc);
+                    }
+                }
+                red[half * 128 + row_in_tile] = acc;
+            }
+            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+            __syncthreads();
+            if (layer == 2 && half == 0) {
+                const int row = tile * 128 + row_in_tile;
+                if (row < M) y[row] = red[row_in_tile] + red[128 + row_in_tile] + red[256];
+            }
+        }
+    }
+    if (!ok) {
+        if (tid == 0) {
+            atomicExch(err, 1u);
+            // give copies and MMAs still in flight a bounded chance to land before TMEM is freed
+            for (long long j = consumed; j < loaded; ++j) {
+                const int b = (int)(j % nbuf);
+                if (mbar_wait(&tma_bar[b], (tma_ph >> b) & 1u)) tma_ph ^= 1u << b;
+            }
+            tc_commit(&drain_bar);   // completes once every MMA this thread issued is done
+            mbar_wait(&drain_bar, 0u);
+        }
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
@@ -321,6 +659,53 @@ cudaError_t launch_gemm_bf16(const void *A, const void *B, const float *bias, fl
     mlp::gemm_bf16_tn_kernel<<<grid, mlp::THREADS, smem, s>>>(
         reinterpret_cast<const __nv_bfloat16 *>(A), reinterpret_cast<const __nv_bfloat16 *>(B), bias, Cf,
         reinterpret_cast<__nv_bfloat16 *>(Cb), M, N, K, relu, err);
+    return cudaGetLastError();
+}
+
+// Whether the fused forward fits: H a multiple of 32 (two column halves of
+// whole 16-column TMEM loads), shared memory for the layouts and 2+ buffers.
+int fused_mlp_nbuf(int I, int H)
+{
+    if (H % 32 != 0 || H > 256 || I > 256) return 0;
+    for (int nb = 4; nb >= 2; --nb)
+        if (mlp::fused_smem(I, H, nb).total <= 220 * 1024) return nb;
+    return 0;
+}
+
+size_t fused_mlp_pack_bytes(int I, int H)
+{
+    const int nch1 = (I + mlp::FKC - 1) / mlp::FKC, nch2 = (H + mlp::FKC - 1) / mlp::FKC;
+    return (size_t)(nch1 + 2 * nch2) * H * mlp::FKC * 2;
+}
+
+cudaError_t launch_fused_pack(const void *w1, const void *w2, const void *w3, int I, int H, void *out, cudaStream_t s)
+{
+    const int nch1 = (I + mlp::FKC - 1) / mlp::FKC, nch2 = (H + mlp::FKC - 1) / mlp::FKC;
+    mlp::fused_pack_kernel<<<128, 256, 0, s>>>(reinterpret_cast<const __nv_bfloat16 *>(w1),
+                                               reinterpret_cast<const __nv_bfloat16 *>(w2),
+                                               reinterpret_cast<const __nv_bfloat16 *>(w3), I, H, nch1, nch2,
+                                               reinterpret_cast<uint4 *>(out));
+    return cudaGetLastError();
+}
+
+cudaError_t launch_fused_mlp_forward(const void *x, int M, int I, int H, const void *wpack, const float *b1,
+                                     const float *b2, const float *b3, const float *w4, const float *b4, float *y,
+                                     unsigned int *err, cudaStream_t s)
+{
+    const int nbuf = fused_mlp_nbuf(I, H);
+    if (nbuf == 0) return cudaErrorInvalidValue;
+    // at least 116 KB: one CTA per SM, so its TMEM allocation never waits on another's
+    const int smem = std::max(mlp::fused_smem(I, H, nbuf).total, 116 * 1024);
+    cudaError_t e = cudaFuncSetAttribute(mlp::fused_mlp_forward_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int ntiles = (M + 127) / 128;
+    const int grid = std::max(1, std::min(ntiles, sms));
+    mlp::fused_mlp_forward_kernel<<<grid, mlp::FTHREADS, smem, s>>>(
+        reinterpret_cast<const __nv_bfloat16 *>(x), M, I, H, reinterpret_cast<const uint4 *>(wpack), b1, b2, b3, w4,
+        b4, y, nbuf, err);
     return cudaGetLastError();
 }
 

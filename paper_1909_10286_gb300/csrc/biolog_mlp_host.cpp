@@ -24,6 +24,12 @@ cudaError_t launch_colsum(const void *x, float *out, int M, int H, cudaStream_t 
 cudaError_t launch_adam(float *w, void *wb, const float *g, float *m, float *v, int n, float lr, float b1, float b2,
                         float eps, int step, cudaStream_t s);
 cudaError_t launch_f32_to_bf16(const float *x, void *y, int n, cudaStream_t s);
+int fused_mlp_nbuf(int I, int H);
+size_t fused_mlp_pack_bytes(int I, int H);
+cudaError_t launch_fused_pack(const void *w1, const void *w2, const void *w3, int I, int H, void *out, cudaStream_t s);
+cudaError_t launch_fused_mlp_forward(const void *x, int M, int I, int H, const void *wpack, const float *b1,
+                                     const float *b2, const float *b3, const float *w4, const float *b4, float *y,
+                                     unsigned int *err, cudaStream_t s);
 }  // namespace biolog
 
 using namespace biolog;
@@ -49,6 +55,11 @@ struct bl_mlp {
     uint16_t *h[3] = {}, *dz = nullptr, *dzt = nullptr, *ht = nullptr, *dh = nullptr;
     float *y = nullptr, *dy = nullptr, *loss = nullptr, *gtmp = nullptr;
     unsigned int *err = nullptr;
+    // inference: BF16 weights of the three layers packed for the fused kernel (repacked
+    // after every change of the weights), or none if the shape does not fit it
+    void *wpack = nullptr;
+    bool packed = false;
+    int fused_nbuf = 0;
     std::vector<void *> allocs;
     std::string msg;
     int lin(int l) const { return l == 0 ? in : H; }
@@ -103,6 +114,28 @@ int upload_params(bl_mlp *m, const std::vector<std::vector<float>> &W, const std
     MK(m, cudaMemcpyAsync(m->w4, w4.data(), w4.size() * 4, cudaMemcpyHostToDevice, m->stream));
     MK(m, cudaMemcpyAsync(m->b4, &b4, 4, cudaMemcpyHostToDevice, m->stream));
     MK(m, cudaStreamSynchronize(m->stream));
+    m->packed = false;
+    return BL_OK;
+}
+
+// inference pass: the fused three-layer kernel where the shape fits it
+int infer(bl_mlp *m, const uint16_t *x, int M, float *y_out)
+{
+    if (m->fused_nbuf == 0) {
+        const uint16_t *a = x;
+        for (int l = 0; l < 3; ++l) {
+            MK(m, launch_gemm_bf16(a, m->wb[l], m->b[l], nullptr, m->h[l], M, m->H, m->lin(l), 1, m->err, m->stream));
+            a = m->h[l];
+        }
+        MK(m, launch_head_forward(m->h[2], m->w4, m->b4, y_out, nullptr, nullptr, nullptr, M, m->H, m->stream));
+        return BL_OK;
+    }
+    if (!m->packed) {
+        MK(m, launch_fused_pack(m->wb[0], m->wb[1], m->wb[2], m->in, m->H, m->wpack, m->stream));
+        m->packed = true;
+    }
+    MK(m, launch_fused_mlp_forward(x, M, m->in, m->H, m->wpack, m->b[0], m->b[1], m->b[2], m->w4, m->b4, y_out,
+                                   m->err, m->stream));
     return BL_OK;
 }
 
@@ -207,6 +240,12 @@ int bl_mlp_create(int32_t in_dim, int32_t hidden, int32_t max_batch, uint64_t se
     if (e == cudaSuccess) e = dalloc(m, &m->dy, (size_t)max_batch);
     if (e == cudaSuccess) e = dalloc(m, &m->loss, (size_t)1);
     if (e == cudaSuccess) e = dalloc(m, &m->err, (size_t)1);
+    m->fused_nbuf = fused_mlp_nbuf(in_dim, hidden);
+    if (e == cudaSuccess && m->fused_nbuf) {
+        uint16_t *wp = nullptr;
+        e = dalloc(m, &wp, fused_mlp_pack_bytes(in_dim, hidden) / 2);
+        m->wpack = wp;
+    }
     if (e != cudaSuccess) {
         g_mlp_error = std::string("cudaMalloc: ") + cudaGetErrorString(e);
         bl_mlp_free(m);
@@ -229,8 +268,9 @@ int bl_mlp_free(bl_mlp *m)
 
 int bl_mlp_forward(bl_mlp *m, const uint16_t *d_x, int32_t M, float *d_y)
 {
-    if (!m || !d_x || !d_y || M < 1 || M > m->max_batch) return BL_EINVAL;
-    return forward(m, d_x, M, d_y, nullptr);
+    if (!m || !d_x || !d_y || M < 1) return BL_EINVAL;
+    if (m->fused_nbuf == 0 && M > m->max_batch) return BL_EINVAL;   // the layer-by-layer path uses the batch buffers
+    return infer(m, d_x, M, d_y);
 }
 
 int bl_mlp_grads(bl_mlp *m, const uint16_t *d_x, const float *d_target, int32_t M, float *h_loss)
@@ -257,6 +297,7 @@ int bl_mlp_train_step(bl_mlp *m, const uint16_t *d_x, const float *d_target, int
     }
     MK(m, launch_adam(m->w4, nullptr, m->gw4, m->mw4, m->vw4, m->H, lr, b1, b2, eps, m->step, m->stream));
     MK(m, launch_adam(m->b4, nullptr, m->gb4, m->mb4, m->vb4, 1, lr, b1, b2, eps, m->step, m->stream));
+    m->packed = false;
     return BL_OK;
 }
 
