@@ -279,14 +279,18 @@ int bl_gemm_bf16(const uint16_t *d_a, const uint16_t *d_b, const float *d_bias, 
 int bl_features(bl_handle *h, int32_t inst, int32_t use_best, uint32_t iter, int32_t i0, int32_t n, uint16_t *d_feat,
                 float *d_base_cost);
 
-/* Algorithm 1 with learned proposals, n_iters times (single-instance handle):
-   per iteration the first `pool` Philox candidates are featurised and ranked
-   by `mlp` (predicted cost change, lower is better); the n_keep best plus a
-   fraction rand_frac of the others, drawn uniformly, are scored exactly by the
-   same kernel as bl_search_step, which takes the argmin and updates the state.
-   Every accepted plan is thus judged by the exact score. pool <= n_cand of the
-   handle; the MLP must have been created on the handle's stream with
-   max_batch >= pool. The first call allocates the pool buffers. */
+/* Algorithm 1 with learned proposals, n_iters times, for every instance of
+   the handle (an extension; the paper draws moves uniformly): per iteration
+   and instance the first `pool` Philox candidates are featurised and ranked
+   by `mlp` (predicted cost change, lower is better) in one pass over all
+   instances; about the n_keep best (threshold from a sample of 4096
+   predictions) plus a fraction rand_frac of the others, drawn uniformly by
+   Philox, are scored exactly by the same kernel as bl_search_step, which takes
+   each instance's argmin and updates its state. Every accepted plan is thus
+   judged by the exact score. pool <= n_cand of the handle; the MLP must have
+   been created on the handle's stream, and pool x instances rows must be
+   within its batch limit (see bl_mlp_forward). The first call allocates the
+   pool buffers (pool x instances x 136 bytes). Asynchronous on the stream. */
 int bl_search_step_learned(bl_handle *h, bl_mlp *mlp, int32_t n_iters, int32_t pool, int32_t n_keep, float rand_frac);
 
 /* Kernel configuration in use: threads per block, grid blocks, candidates

@@ -937,7 +937,6 @@ int bl_search_step_learned(bl_handle *h, bl_mlp *mlp, int32_t n_iters, int32_t p
     if (!h || !mlp || n_iters < 0 || pool < 1 || n_keep < 1 || n_keep > pool || !(rand_frac >= 0.f && rand_frac <= 1.f))
         return BL_EINVAL;
     if (h->failed) return BL_ESTATE;
-    if (h->n_inst != 1) { h->err = "learned proposals: one instance per handle"; return BL_EINVAL; }
     if (mlp_stream_of(mlp) != h->stream) {
         h->err = "learned proposals: create the MLP on the search handle's stream";
         return BL_EINVAL;
@@ -946,27 +945,32 @@ int bl_search_step_learned(bl_handle *h, bl_mlp *mlp, int32_t n_iters, int32_t p
         h->err = "learned proposals: pool must not exceed the handle's n_cand (the work decomposition)";
         return BL_EINVAL;
     }
+    const int nb = h->n_inst;
+    const size_t rows = (size_t)pool * nb;
     if (h->learned_pool < pool) {
         if (h->l_feat) { cudaFree(h->l_feat); cudaFree(h->l_y); cudaFree(h->l_list); cudaFree(h->l_count); }
-        CK(h, cudaMalloc((void **)&h->l_feat, (size_t)pool * NFEAT * 2));
-        CK(h, cudaMalloc((void **)&h->l_y, (size_t)pool * 4));
-        CK(h, cudaMalloc((void **)&h->l_list, (size_t)pool * 4));
-        CK(h, cudaMalloc((void **)&h->l_count, 16));
-        h->l_thresh = reinterpret_cast<float *>(h->l_count + 2);
+        h->l_feat = nullptr; h->l_y = nullptr; h->l_list = nullptr; h->l_count = nullptr; h->learned_pool = 0;
+        CK(h, cudaMalloc((void **)&h->l_feat, rows * NFEAT * 2));
+        CK(h, cudaMalloc((void **)&h->l_y, rows * 4));
+        CK(h, cudaMalloc((void **)&h->l_list, rows * 4));
+        CK(h, cudaMalloc((void **)&h->l_count, (size_t)nb * 8));   // counts, then thresholds
+        h->l_thresh = reinterpret_cast<float *>(h->l_count + nb);
         h->learned_pool = pool;
     }
+    if (rows > (size_t)INT32_MAX) { h->err = "learned proposals: pool x instances exceeds 2^31 rows"; return BL_ETOO_LARGE; }
     for (int it = 0; it < n_iters; ++it) {
-        // the iteration's base (Eq. 5) and counter are read on the device by every kernel
+        // each instance's base (Eq. 5) and counter are read on the device by every kernel;
+        // instance b's pool occupies rows [b * pool, (b + 1) * pool)
         CK(h, launch_features(h->cfg, h->at<InstMeta>(h->ws.meta), 0, -1, 0xffffffffu, 0, pool, h->sp, h->l_feat,
-                              nullptr, h->stream));
-        int rc = bl_mlp_forward(mlp, h->l_feat, pool, h->l_y);
+                              nullptr, h->stream, nb));
+        int rc = bl_mlp_forward(mlp, h->l_feat, (int32_t)rows, h->l_y);
         if (rc != BL_OK) { h->err = "learned proposals: MLP forward failed"; return rc; }
         CK(h, launch_select(h->l_y, pool, n_keep, rand_frac, 0x9E37u + h->learned_iters++, h->l_list, h->l_count,
-                            h->l_thresh, h->stream));
+                            h->l_thresh, nb, h->stream));
         CK(h, launch_search_iteration(h->cfg, h->at<InstMeta>(h->ws.meta), h->at<WorkItem>(h->ws.work),
                                       (int32_t)h->work.size(), h->sp, h->at<unsigned long long>(h->ws.slot_key),
                                       h->at<float>(h->ws.slot_tmax), h->at<int32_t>(h->ws.slot_base), h->stream,
-                                      h->l_list, h->l_count));
+                                      h->l_list, h->l_count, pool));
     }
     return BL_OK;
 }

@@ -117,13 +117,14 @@ struct LaunchCfg {
 cudaError_t launch_search_iteration(const LaunchCfg &cfg, const InstMeta *d_meta, const WorkItem *d_work,
                                     int32_t n_work, SearchParams prm, unsigned long long *slot_key,
                                     float *slot_tmax, const int32_t *slot_base, cudaStream_t s,
-                                    const uint32_t *cand_list = nullptr, const int32_t *cand_count = nullptr);
+                                    const uint32_t *cand_list = nullptr, const int32_t *cand_count = nullptr,
+                                    int32_t list_stride = 0);
 constexpr int NFEAT = 64;   // features per candidate move
 cudaError_t launch_features(const LaunchCfg &cfg, const InstMeta *d_meta, int32_t inst, int32_t use_best,
                             uint32_t iter, int32_t i0, int32_t n, SearchParams prm, uint16_t *d_feat,
-                            float *d_base_cost, cudaStream_t s);
+                            float *d_base_cost, cudaStream_t s, int32_t n_batch = 0);
 cudaError_t launch_select(const float *d_y, int32_t P, int32_t n_keep, float rand_frac, uint32_t salt,
-                          uint32_t *d_list, int32_t *d_count, float *d_thresh, cudaStream_t s);
+                          uint32_t *d_list, int32_t *d_count, float *d_thresh, int32_t n_batch, cudaStream_t s);
 cudaError_t launch_score_dump(const LaunchCfg &cfg, const InstMeta *d_meta, int32_t inst, int32_t use_best,
                               uint32_t iter, float tmax_star, int32_t i0, int32_t n, int32_t identity,
                               SearchParams prm, float *d_cost, float *d_tmax, int16_t *d_moves, int16_t *d_nhu,

@@ -30,6 +30,7 @@
 #include <type_traits>
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include "biolog_internal.h"
 
 namespace biolog {
@@ -1098,15 +1099,14 @@ __global__ void __launch_bounds__(SH::NT, SH::MINB) search_iteration_kernel(cons
                                                                   float *__restrict__ slot_tmax,
                                                                   const int32_t *__restrict__ slot_base,
                                                                   const uint32_t *__restrict__ cand_list,
-                                                                  const int32_t *__restrict__ cand_count)
+                                                                  const int32_t *__restrict__ cand_count,
+                                                                  int32_t list_stride)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ BlockShared bs;
     const int tid = threadIdx.x;
     const int lane = tid & 31, warp = tid >> 5;
     constexpr int NT = SH::NT;
-    // list mode (learned proposals): positions index a list of candidate numbers
-    const int list_n = cand_list ? *cand_count : 0;
     if (tid == 0) {
         mbar_init(&bs.mbar, 1);
         fence_mbar_init();
@@ -1128,6 +1128,9 @@ __global__ void __launch_bounds__(SH::NT, SH::MINB) search_iteration_kernel(cons
         }
         const float tmax_star = M.state->tmaxstar;
         const uint32_t iter = bs.iter;
+        // list mode (learned proposals): positions index instance wi.inst's list of candidate numbers
+        const int list_n = cand_list ? cand_count[wi.inst] : 0;
+        const uint32_t *ilist = cand_list ? cand_list + (size_t)wi.inst * list_stride : nullptr;
         // list mode: the kept candidates are dealt evenly over the instance's work items
         // (a multiple of 32 each), whatever the tile the full pool was planned with
         const int tl = cand_list ? max(32, ((min(M.n_cand, list_n) + M.n_tiles - 1) / M.n_tiles + 31) & ~31) : M.tile;
@@ -1141,7 +1144,7 @@ __global__ void __launch_bounds__(SH::NT, SH::MINB) search_iteration_kernel(cons
             // (c1 may be below c0 in list mode: then the work item only reports an empty slot)
             if (base < c1) {
                 const int pos = base + lane;
-                const int i = (cand_list && pos < c1) ? (int)cand_list[pos] : pos;
+                const int i = (ilist && pos < c1) ? (int)ilist[pos] : pos;
                 bool feas = false;
                 MoveRec m = {4, 0, 0, 0};
                 if (pos < c1) {
@@ -1348,11 +1351,17 @@ template <class SH>
 __global__ void __launch_bounds__(SH::NT) features_kernel(const InstMeta *__restrict__ meta, int32_t inst,
                                                           int32_t use_best, uint32_t iter, int32_t i0, int32_t n,
                                                           SearchParams prm, SmemPlan sp, __nv_bfloat16 *__restrict__ feat,
-                                                          float *__restrict__ base_cost)
+                                                          float *__restrict__ base_cost, int32_t batched)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ BlockShared bs;
     const int tid = threadIdx.x, nt = blockDim.x;
+    // batched: grid row y serves instance y, whose n rows start at row y * n
+    if (batched) {
+        inst = (int32_t)blockIdx.y;
+        feat += (size_t)inst * n * NFEAT;
+        if (base_cost) base_cost += inst;
+    }
     if (tid == 0) {
         mbar_init(&bs.mbar, 1);
         fence_mbar_init();
@@ -1496,6 +1505,8 @@ __global__ void __launch_bounds__(SH::NT) features_kernel(const InstMeta *__rest
 __global__ void select_threshold_kernel(const float *__restrict__ y, int32_t P, int32_t n_keep, float *__restrict__ thresh)
 {
     __shared__ float sbuf[4096];
+    y += (size_t)blockIdx.x * P;   // block b: instance b of a batch
+    thresh += blockIdx.x;
     const int S = 4096;
     for (int j = threadIdx.x; j < S; j += blockDim.x) {
         const long long idx = (long long)j * P / S;
@@ -1528,12 +1539,18 @@ __global__ void select_compact_kernel(const float *__restrict__ y, int32_t P, co
                                       float rand_frac, uint32_t salt, uint32_t *__restrict__ list,
                                       int32_t *__restrict__ count)
 {
+    // grid row b: instance b of a batch (its own predictions, threshold, list and count)
+    const uint32_t b = blockIdx.y;
+    y += (size_t)b * P;
+    list += (size_t)b * P;
+    thresh += b;
+    count += b;
     const float th = *thresh;
     const uint32_t cut = (uint32_t)(rand_frac * 4294967295.0f);
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < P; i += gridDim.x * blockDim.x) {
         bool keep = y[i] <= th;
         if (!keep) {
-            uint32_t r[4] = {(uint32_t)i, salt, 0x5E1EC7u, 2u};
+            uint32_t r[4] = {(uint32_t)i, salt, 0x5E1EC7u + b, 2u};
             philox10(r, 0x243F6A88u, 0x85A308D3u);
             keep = r[0] < cut;
         }
@@ -1732,21 +1749,21 @@ cudaError_t configure_kernels(int32_t shape, size_t smem)
 cudaError_t launch_search_iteration(const LaunchCfg &cfg, const InstMeta *d_meta, const WorkItem *d_work,
                                     int32_t n_work, SearchParams prm, unsigned long long *slot_key, float *slot_tmax,
                                     const int32_t *slot_base, cudaStream_t s, const uint32_t *cand_list,
-                                    const int32_t *cand_count)
+                                    const int32_t *cand_count, int32_t list_stride)
 {
     const SmemPlan sp = plan_for(cfg);
     switch (cfg.shape) {
     case SHAPE_T4_S64_DSMEM:
         search_iteration_kernel<ShapeA><<<cfg.grid, ShapeA::NT, sp.total, s>>>(
-            d_meta, d_work, n_work, prm, sp, slot_key, slot_tmax, slot_base, cand_list, cand_count);
+            d_meta, d_work, n_work, prm, sp, slot_key, slot_tmax, slot_base, cand_list, cand_count, list_stride);
         break;
     case SHAPE_T8_S64_DSMEM:
         search_iteration_kernel<ShapeB><<<cfg.grid, ShapeB::NT, sp.total, s>>>(
-            d_meta, d_work, n_work, prm, sp, slot_key, slot_tmax, slot_base, cand_list, cand_count);
+            d_meta, d_work, n_work, prm, sp, slot_key, slot_tmax, slot_base, cand_list, cand_count, list_stride);
         break;
     default:
         search_iteration_kernel<ShapeC><<<cfg.grid, ShapeC::NT, sp.total, s>>>(
-            d_meta, d_work, n_work, prm, sp, slot_key, slot_tmax, slot_base, cand_list, cand_count);
+            d_meta, d_work, n_work, prm, sp, slot_key, slot_tmax, slot_base, cand_list, cand_count, list_stride);
     }
     return cudaGetLastError();
 }
@@ -1812,12 +1829,15 @@ cudaError_t launch_argmin_noalloc(const LaunchCfg &cfg, const InstMeta *d_meta, 
 
 cudaError_t launch_features(const LaunchCfg &cfg, const InstMeta *d_meta, int32_t inst, int32_t use_best,
                             uint32_t iter, int32_t i0, int32_t n, SearchParams prm, uint16_t *d_feat,
-                            float *d_base_cost, cudaStream_t s)
+                            float *d_base_cost, cudaStream_t s, int32_t n_batch)
 {
     const SmemPlan sp = plan_for(cfg);
     const int nt = threads_of(cfg.shape);
+    const int batched = n_batch > 0 ? 1 : 0;
+    const int gy = batched ? n_batch : 1;
     int grid = (n + nt - 1) / nt;
-    if (grid > cfg.grid) grid = cfg.grid;
+    const int cap = std::max(1, cfg.grid / gy);   // about one resident wave over all instances
+    if (grid > cap) grid = cap;
     if (grid < 1) grid = 1;
     __nv_bfloat16 *f = reinterpret_cast<__nv_bfloat16 *>(d_feat);
     cudaError_t e;
@@ -1825,29 +1845,30 @@ cudaError_t launch_features(const LaunchCfg &cfg, const InstMeta *d_meta, int32_
     case SHAPE_T4_S64_DSMEM:
         e = cudaFuncSetAttribute(features_kernel<ShapeA>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sp.total);
         if (e == cudaSuccess)
-            features_kernel<ShapeA><<<grid, nt, sp.total, s>>>(d_meta, inst, use_best, iter, i0, n, prm, sp, f, d_base_cost);
+            features_kernel<ShapeA><<<dim3(grid, gy), nt, sp.total, s>>>(d_meta, inst, use_best, iter, i0, n, prm, sp, f, d_base_cost, batched);
         break;
     case SHAPE_T8_S64_DSMEM:
         e = cudaFuncSetAttribute(features_kernel<ShapeB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sp.total);
         if (e == cudaSuccess)
-            features_kernel<ShapeB><<<grid, nt, sp.total, s>>>(d_meta, inst, use_best, iter, i0, n, prm, sp, f, d_base_cost);
+            features_kernel<ShapeB><<<dim3(grid, gy), nt, sp.total, s>>>(d_meta, inst, use_best, iter, i0, n, prm, sp, f, d_base_cost, batched);
         break;
     default:
         e = cudaFuncSetAttribute(features_kernel<ShapeC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sp.total);
         if (e == cudaSuccess)
-            features_kernel<ShapeC><<<grid, nt, sp.total, s>>>(d_meta, inst, use_best, iter, i0, n, prm, sp, f, d_base_cost);
+            features_kernel<ShapeC><<<dim3(grid, gy), nt, sp.total, s>>>(d_meta, inst, use_best, iter, i0, n, prm, sp, f, d_base_cost, batched);
     }
     if (e != cudaSuccess) return e;
     return cudaGetLastError();
 }
 
 cudaError_t launch_select(const float *d_y, int32_t P, int32_t n_keep, float rand_frac, uint32_t salt,
-                          uint32_t *d_list, int32_t *d_count, float *d_thresh, cudaStream_t s)
+                          uint32_t *d_list, int32_t *d_count, float *d_thresh, int32_t n_batch, cudaStream_t s)
 {
-    cudaError_t e = cudaMemsetAsync(d_count, 0, sizeof(int32_t), s);
+    cudaError_t e = cudaMemsetAsync(d_count, 0, sizeof(int32_t) * (size_t)n_batch, s);
     if (e != cudaSuccess) return e;
-    select_threshold_kernel<<<1, 1024, 0, s>>>(d_y, P, n_keep, d_thresh);
-    select_compact_kernel<<<592, 256, 0, s>>>(d_y, P, d_thresh, rand_frac, salt, d_list, d_count);
+    select_threshold_kernel<<<n_batch, 1024, 0, s>>>(d_y, P, n_keep, d_thresh);
+    const int gx = std::max(1, std::min(592, (P + 255) / 256));
+    select_compact_kernel<<<dim3(gx, n_batch), 256, 0, s>>>(d_y, P, d_thresh, rand_frac, salt, d_list, d_count);
     return cudaGetLastError();
 }
 

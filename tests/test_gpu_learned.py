@@ -94,11 +94,35 @@ def test_features_state_sentinel_matches_explicit():
     S.close()
 
 
+def _replay_want(S, net, inst_k, k, it, use_best, tmaxstar, pool, n_keep, rf, salt):
+    """The learned iteration's choice for instance k, recomputed on the host from
+    the library's own features, the same network and exact costs."""
+    import torch
+
+    feat = torch.empty((pool, 64), dtype=torch.bfloat16, device="cuda")
+    S.features(use_best, it, 0, pool, feat, inst=k)
+    y = net.forward(feat).cpu().numpy()
+    S_ = 4096
+    sample = np.sort(np.array([y[j * pool // S_] for j in range(S_)], dtype=np.float32))
+    th = sample[min(S_ - 1, n_keep * S_ // pool)]
+    cut = np.uint32(np.float32(rf) * np.float32(4294967295.0))
+    keep = []
+    for i in range(pool):
+        if y[i] <= th:
+            keep.append(i)
+        else:
+            r = O.philox4x32_10([i, salt, 0x5E1EC7 + k, 2], [0x243F6A88, 0x85A308D3])
+            if r[0] < cut:
+                keep.append(i)
+    g = S.score_candidates(use_best, it, tmaxstar, 0, pool, inst=k)
+    keys = [(np.float32(g["cost"][i]).view(np.uint32), i) for i in keep]
+    return min(keys), len(keep)
+
+
 def test_learned_step_matches_host_replay():
     """One learned iteration equals: rank the pool with the same network, keep the
     predicted best (threshold from the same 4096-prediction sample) plus the
     Philox-drawn random fallback, score those exactly, take the argmin."""
-    import torch
     from paper_1909_10286_gb300.mlp import MLP
 
     inst = I.make_instance("paper", 4)
@@ -111,24 +135,8 @@ def test_learned_step_matches_host_replay():
     o = O.Oracle(inst)
     use_best = int(o.eps_select(op, it))
     net = MLP(64, 256, max_batch=pool, seed=7, stream=S.stream)
-    feat = torch.empty((pool, 64), dtype=torch.bfloat16, device="cuda")
-    S.features(use_best, it, 0, pool, feat)
-    y = net.forward(feat).cpu().numpy()
-    S_ = 4096
-    sample = np.sort(np.array([y[j * pool // S_] for j in range(S_)], dtype=np.float32))
-    th = sample[min(S_ - 1, n_keep * S_ // pool)]
-    cut = np.uint32(np.float32(rf) * np.float32(4294967295.0))
-    keep = []
-    for i in range(pool):
-        if y[i] <= th:
-            keep.append(i)
-        else:
-            r = O.philox4x32_10([i, 0x9E37, 0x5E1EC7, 2], [0x243F6A88, 0x85A308D3])
-            if r[0] < cut:
-                keep.append(i)
-    g = S.score_candidates(use_best, it, st["tmaxstar"], 0, pool)
-    keys = [(np.float32(g["cost"][i]).view(np.uint32), i) for i in keep]
-    want = min(keys)
+    want, n_kept = _replay_want(S, net, inst, 0, it, use_best, st["tmaxstar"], pool, n_keep, rf, 0x9E37)
+    assert n_keep < n_kept < pool // 2
     S.search_step_learned(net, 1, pool, n_keep, rf)
     log = S.get_log(it, 1)
     assert int(log["istar"][0]) == want[1]
@@ -138,6 +146,33 @@ def test_learned_step_matches_host_replay():
     new = S.get_state()
     if np.isfinite(c):
         assert o.score(gpu_plan(new, "xold"), gate=0)["cost"] == pytest.approx(c, rel=REL_TOL)
+    net.close()
+    S.close()
+
+
+def test_batched_learned_step_matches_per_instance_replay():
+    """A batched handle ranks all instances' pools in one pass; each instance's
+    choice equals its own replay (its base, its threshold, its fallback draws)."""
+    from paper_1909_10286_gb300.mlp import MLP
+
+    insts = I.make_batch("paper", [3, 5, 8])
+    pool, n_keep, rf = 8192, 1500, 0.05
+    S = biolog.Search(insts, biolog.make_params(n_cand=pool, eps=0.5, seed=1001, gate=1))
+    S.search_step(2)
+    net = MLP(64, 256, max_batch=pool * len(insts), seed=9, stream=S.stream)
+    S.search_step_learned(net, 1, pool, n_keep, rf)   # salt 0x9E37; the next call uses 0x9E38
+    op = O.make_params(eps=0.5, seed=1001, gate=1)
+    wants = []
+    for k, inst in enumerate(insts):
+        st = S.get_state(inst=k)
+        it = st["iter"]
+        use_best = int(O.Oracle(inst).eps_select(op, it))
+        wants.append((it, _replay_want(S, net, inst, k, it, use_best, st["tmaxstar"], pool, n_keep, rf, 0x9E38)[0]))
+    S.search_step_learned(net, 1, pool, n_keep, rf)
+    for k, (it, want) in enumerate(wants):
+        log = S.get_log(it, 1, inst=k)
+        assert int(log["istar"][0]) == want[1], k
+        assert float(log["c_istar"][0]) == float(np.uint32(want[0]).view(np.float32)), k
     net.close()
     S.close()
 
