@@ -39,6 +39,14 @@ WORKLOAD = "paper-scale plain search: 40 fields, 5 BPs, 3 tours, 10 HUs, 20 SUs,
 WORKLOAD_BATCHED = ("batched uneven instances: 256 instances (fields U{10..120}, BPs U{2..10}, tours U{1..6}, "
                     "HUs U{2..20}, SUs U{4..40}), 2^16 candidates/instance/iter, one launch per iteration")
 L2_FLUSH_BYTES = 256 << 20
+# time-to-1% study settings per workload (paper: seeds 0-9, the paper's 10 experiments)
+STUDY = {
+    "paper": dict(workload="paper", seeds=range(10), n=1 << 20, iters=300, budget=1000, n_batched=1 << 16,
+                  pool=1 << 16, keep=7373, rand_frac=0.014, train_seeds=range(100, 110)),
+    "large": dict(workload="large", seeds=range(5), n=1 << 20, iters=400, budget=400, n_batched=1 << 16,
+                  pool=1 << 18, keep=2359, rand_frac=0.001, train_seeds=range(100, 104), train_iters=30,
+                  ref_n=1 << 16),
+}
 
 
 def _dist():
@@ -198,11 +206,23 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--n-inst", type=int, default=256, help="instances of the batched workload")
     ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--no-time-to-target", action="store_true",
+                    help="skip the time-to-1%% study (paper workload, rank 0, one GPU)")
+    ap.add_argument("--study", action="store_true", help="print only the time-to-1%% study for --workload")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     ws, rank, local = _dist()
     if args.impl == "reference":
         run_reference(args, ws, rank)
+        return
+    if args.study:
+        import torch
+
+        from paper_1909_10286_gb300 import time_to_target
+
+        torch.cuda.set_device(local)
+        print(json.dumps(dict(study="time to within 1% of the best cost",
+                              **time_to_target.study(**STUDY[args.workload]))), flush=True)
         return
 
     import numpy as np
@@ -315,8 +335,27 @@ def main():
             line["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": thr, "kind": "oracle",
                                     "sample": f"{iters} oracle iterations of {m_s} candidates (of {n}) from the "
                                               "initial plan"}
+        S.close()
+        if ws == 1 and args.workload == "paper" and not args.no_time_to_target:
+            from paper_1909_10286_gb300 import time_to_target
+
+            r = time_to_target.study(**STUDY["paper"])
+            line["time_to_1pct"] = {
+                "unit": "ms", "higher_is_better": False, "tol": r["tol"], "instances": r["seeds"],
+                "c_ref": "best C* of a plain run of 10x the 1000-iteration budget, 2^20 candidates/iter",
+                "median_ms": {k: f["median_ms"] for k, f in r["forms"].items()},
+                "all_instances_ms": {k: f["all_instances_ms"] for k, f in r["forms"].items()},
+                "ms_per_iter": {k: f["ms_per_iter"] for k, f in r["forms"].items()},
+                "iters_to_target": {k: f["iters"] for k, f in r["forms"].items()},
+                "forms": {"plain": "one instance per handle, 2^20 candidates/iter",
+                          "batched": "10 instances in one handle, 2^16 candidates/instance/iter",
+                          "learned_batched": "10 instances in one handle; per instance 2^16 Philox moves ranked "
+                                             "by the MLP, ~7373 best + 1.4% random scored exactly"},
+                "ranker_training": {k: r["forms"]["learned_batched"][k]
+                                    for k in ("train_tuples", "train_s", "train_loss_first_last")}}
         print(json.dumps(line), flush=True)
-    S.close()
+    else:
+        S.close()
     if ws > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
