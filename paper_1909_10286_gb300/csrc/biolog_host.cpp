@@ -588,11 +588,8 @@ int init_common(const bl_instance *insts, int32_t n_inst, const bl_params *param
         CK(nullptr, cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
         cudaError_t e = configure_kernels(shape, h->cfg.smem);
         if (e != cudaSuccess) { delete h; return cuda_fail(nullptr, e, "configure_kernels"); }
-        int smem_per_sm = 0;
-        CK(nullptr, cudaDeviceGetAttribute(&smem_per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev));
-        bps = std::max(1, std::min(smem_per_sm / (int)(h->cfg.smem + 1024), 2048 / h->cfg.threads));
-        bps = std::min(bps, 65536 / (h->cfg.threads * 128));   // register budget of the scorer
-        bps = std::max(bps, 1);
+        // as many blocks per SM as registers and shared memory allow
+        bps = std::max(1, search_blocks_per_sm(shape, h->cfg.smem));
         if (params->blocks_per_sm > 0) bps = params->blocks_per_sm;
     } else {
         bps = std::max(1, params->blocks_per_sm);

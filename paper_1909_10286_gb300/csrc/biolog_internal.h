@@ -139,6 +139,7 @@ cudaError_t launch_argmin_noalloc(const LaunchCfg &cfg, const InstMeta *d_meta, 
 size_t shared_bytes(int32_t shape, int32_t threads, int32_t max_prefix, int32_t max_plan_len, int32_t max_F,
                     int32_t max_B, int32_t max_T);
 cudaError_t configure_kernels(int32_t shape, size_t smem);
+int search_blocks_per_sm(int32_t shape, size_t smem);
 int max_tours_of(int32_t shape);
 int threads_of(int32_t shape);
 int max_su_of(int32_t shape);

@@ -131,13 +131,13 @@ struct Shape {
 };
 
 #ifndef BIOLOG_SHAPEA_MINB
-#define BIOLOG_SHAPEA_MINB 2
+#define BIOLOG_SHAPEA_MINB 3
 #endif
 using ShapeA = Shape<4, 0, true, 256, BIOLOG_SHAPEA_MINB>;   // <= 4 tours, <= 32 HUs/SUs, 32-bit sums
 using ShapeB = Shape<8, 1, true, 128, 4>;                     // <= 8 tours, <= 64 HUs/SUs
 using ShapeC = Shape<16, 2, false, 128, 2>;                   // <= 16 tours, <= 128 SUs, distances via L2
 
-constexpr int NF32 = 8;   // per-tour floats: LHU, LSU, A, DB2 (2 Dbar), Tc, Tw, 1/R, shuttle ratio
+constexpr int NF32 = 5;   // per-tour floats: LHU, LSU, A, DB2 (2 Dbar), 1/R
 constexpr int WQ = 64;    // per-warp queue of feasible candidates (ring buffer)
 
 template <typename M>
@@ -498,50 +498,57 @@ struct ScoreOut {
     float cost, tmax;
 };
 
-// Per-thread per-tour state: one shared-memory column per value.
+// Per-thread per-tour state: one shared-memory column per value. (Completion
+// and waiting times live in registers during the local minimisations; the
+// per-tour report of the inspection kernel keeps its own copies.)
 template <class SH>
 struct TourState {
     static constexpr int MAXT = SH::MAXT, NT = SH::NT;
     using M = typename SH::Mask;
     using S = typename SH::Sum;
-    Col<float, NT> LHU, LSU, A, DB2, Tc, Tw, iR, KF;
+    Col<float, NT> LHU, LSU, A, DB2, iR;
     Col<int, NT> star;
     Col<S, NT> Rq, Saq;
     Col<M, NT> Hm, S0;
-    Col<unsigned long long, NT> S1, Sh;
+    Col<unsigned long long, NT> S1;
     __device__ __forceinline__ void bind(unsigned char *base, int tid)
     {
         constexpr int C = MAXT * NT;
         float *f = (float *)base + tid;
-        LHU.p = f; LSU.p = f + C; A.p = f + 2 * C; DB2.p = f + 3 * C; Tc.p = f + 4 * C; Tw.p = f + 5 * C;
-        iR.p = f + 6 * C; KF.p = f + 7 * C;
+        LHU.p = f; LSU.p = f + C; A.p = f + 2 * C; DB2.p = f + 3 * C; iR.p = f + 4 * C;
         int *i = (int *)base + (size_t)NF32 * C + tid;
         star.p = i;
         S *q = (S *)((int *)base + (size_t)(NF32 + 1) * C) + tid;
         Rq.p = q; Saq.p = q + C;
         M *m = (M *)((S *)((int *)base + (size_t)(NF32 + 1) * C) + 2 * C) + tid;
         Hm.p = m; S0.p = m + C;
-        unsigned long long *w = (unsigned long long *)((M *)((S *)((int *)base + (size_t)(NF32 + 1) * C) + 2 * C) + 2 * C) + tid;
-        S1.p = w; Sh.p = w + C;
+        // the second SU mask word exists only for sets of more than 64 SUs
+        S1.p = (unsigned long long *)((M *)((S *)((int *)base + (size_t)(NF32 + 1) * C) + 2 * C) + 2 * C) + tid;
     }
     __host__ __device__ static constexpr size_t bytes()
     {
         constexpr size_t C = (size_t)MAXT * NT;
-        return (NF32 + 1) * C * 4 + 2 * C * sizeof(S) + 2 * C * sizeof(M) + 2 * C * 8;
+        return (NF32 + 1) * C * 4 + 2 * C * sizeof(S) + 2 * C * sizeof(M) + (SH::SW > 1 ? C * 8 : 0);
     }
 };
 
-// Per-candidate scoring.
-template <class SH, bool DUMP>
+// Per-candidate scoring. DUMP: the inspection kernel's full per-tour report;
+// IDENT: the base plan's own T_compl, shuttle ratio and shuttle sum per active
+// tour (o_tc, o_kf, o_sh), written without local arrays.
+template <class SH, bool DUMP, bool IDENT = false>
 __device__ ScoreOut score_candidate(const Ctx &c, const SearchParams &p, const MoveRec &m, float tmax_star,
                                     unsigned char *tstate, int tid, int16_t *o_nhu, int16_t *o_nsu, float *o_tc,
-                                    float *o_tw, float *o_tcost, int16_t *o_hu, int16_t *o_su)
+                                    float *o_tw, float *o_tcost, int16_t *o_hu, int16_t *o_su, float *o_kf = nullptr,
+                                    long long *o_sh = nullptr)
 {
     constexpr int MAXT = SH::MAXT, SW = SH::SW;
     using M = typename SH::Mask;
     using S = typename SH::Sum;
     TourState<SH> ts;
     ts.bind(tstate, tid);
+    // per-tour report (DUMP only): completion and waiting times, shuttle sums
+    [[maybe_unused]] float dTc[MAXT], dTw[MAXT];
+    [[maybe_unused]] long long dSh[MAXT];
 #define FOR_ACTIVE(g) _Pragma("unroll") for (int g = 0; g < MAXT; ++g) if ((amask >> g) & 1u)
     ScoreOut out;
     View x;
@@ -582,7 +589,6 @@ __device__ ScoreOut score_candidate(const Ctx &c, const SearchParams &p, const M
             ts.Rq.set(g, rq);
             const float R = __fmul_rn(to_f(rq), c.rqs);
             const float t = __fmaf_rn(ts.LHU.get(g), c.inv_v, __fdividef(ts.A.get(g), R));
-            ts.Tc.set(g, t);
             tv[g] = t;
             ++j;
         }
@@ -624,7 +630,6 @@ __device__ ScoreOut score_candidate(const Ctx &c, const SearchParams &p, const M
             ts.Hm.set(gx, ts.Hm.get(gx) | bit);
             ts.Hm.set(gn, mn & ~bit);
             ts.Rq.set(gx, nqx); ts.Rq.set(gn, nqn);
-            ts.Tc.set(gx, tmx); ts.Tc.set(gn, tmn);
 #pragma unroll
             for (int g = 0; g < MAXT; ++g) tv[g] = (g == gx) ? tmx : ((g == gn) ? tmn : tv[g]);
         }
@@ -633,6 +638,13 @@ __device__ ScoreOut score_candidate(const Ctx &c, const SearchParams &p, const M
     {
         bool first = true;
         FOR_ACTIVE(g) { tmax = first ? tv[g] : fmaxf(tmax, tv[g]); first = false; }
+    }
+    if constexpr (DUMP) {
+#pragma unroll
+        for (int g = 0; g < MAXT; ++g) dTc[g] = tv[g];
+    }
+    if constexpr (IDENT) {
+        FOR_ACTIVE(g) o_tc[g] = tv[g];
     }
 
     // --- SU assignment (Algorithm 2, Eq. 6). R(g) is fixed now: one reciprocal per tour.
@@ -651,7 +663,6 @@ __device__ ScoreOut score_candidate(const Ctx &c, const SearchParams &p, const M
             ts.star.set(g, st);
             const float fill = __fmul_rn(to_f((S)(sq - (S)c.sufq[st])), c.fqs);
             const float t = __fmaf_rn(-fill, ir, __fmul_rn(ts.DB2.get(g), c.suinv[st]));
-            ts.Tw.set(g, t);
             tv[g] = t;
             ++j;
         }
@@ -722,10 +733,14 @@ __device__ ScoreOut score_candidate(const Ctx &c, const SearchParams &p, const M
             }
             ts.Saq.set(gx, (S)(sqx + (S)c.sufq[k])); ts.Saq.set(gn, (S)(sqn - (S)c.sufq[k]));
             ts.star.set(gx, sx); ts.star.set(gn, sn);
-            ts.Tw.set(gx, tmx); ts.Tw.set(gn, tmn);
 #pragma unroll
             for (int g = 0; g < MAXT; ++g) tv[g] = (g == gx) ? tmx : ((g == gn) ? tmn : tv[g]);
         }
+    }
+
+    if constexpr (DUMP) {
+#pragma unroll
+        for (int g = 0; g < MAXT; ++g) dTw[g] = tv[g];
     }
 
     // --- path-length cost (Sec. 2.2, Eq. 4). Shuttle sums in fixed point are exact, so the
@@ -741,7 +756,7 @@ __device__ ScoreOut score_candidate(const Ctx &c, const SearchParams &p, const M
             const unsigned long long s1 = (SW > 1) ? ts.S1.get(g) : 0ull;
             const int nsu = popc_m(s0) + (SW > 1 ? popc_m(s1) : 0);
             kfv[g] = __fdividef((float)nsu, __fmul_rn(__ll2float_rn(cap_sum<SH>(c, s0, s1)), c.cqs));
-            ts.KF.set(g, kfv[g]);
+            if constexpr (IDENT) o_kf[g] = kfv[g];
         }
     }
     // A tour's shuttle sum is exact and depends only on its fields, their BPs and its
@@ -773,7 +788,8 @@ __device__ ScoreOut score_candidate(const Ctx &c, const SearchParams &p, const M
     for (int g = 0; g < c.T; ++g) {
         if (!((amask >> g) & 1u)) continue;
         const long long v0 = ((fresh >> g) & 1u) ? 0ll : c.sh_base[g];
-        ts.Sh.set(g, (unsigned long long)v0);
+        if constexpr (DUMP) dSh[g] = v0;
+        if constexpr (IDENT) o_sh[g] = v0;
         shq += v0;
     }
     if (fresh) {
@@ -793,7 +809,8 @@ __device__ ScoreOut score_candidate(const Ctx &c, const SearchParams &p, const M
                 acc += (long long)n * (long long)c.dqown[kk];
             }
             shq += acc;
-            ts.Sh.set(g, ts.Sh.get(g) + (unsigned long long)acc);
+            if constexpr (DUMP) dSh[g] += acc;
+            if constexpr (IDENT) o_sh[g] += acc;
         }
         int mv_f0 = -1, mv_f1 = -1;
         if (x.kind == 0 && x.sg != x.dg) mv_f0 = x.v;
@@ -811,7 +828,8 @@ __device__ ScoreOut score_candidate(const Ctx &c, const SearchParams &p, const M
                 const int n = ceil_n(g, c.supply[f], kf);
                 const long long a = (long long)n * c.dq(1 + c.B + f, 1 + b);
                 shq += a;
-                ts.Sh.set(g, ts.Sh.get(g) + (unsigned long long)a);
+                if constexpr (DUMP) dSh[g] += a;
+                if constexpr (IDENT) o_sh[g] += a;
             }
         }
     }
@@ -825,13 +843,14 @@ __device__ ScoreOut score_candidate(const Ctx &c, const SearchParams &p, const M
         const int nsu = popc_m(s0) + (SW > 1 ? popc_m(s1) : 0);
         const float route = __fadd_rn(__fmul_rn((float)nhu, ts.LHU.get(g)), __fmul_rn((float)nsu, ts.LSU.get(g)));
         cost = __fadd_rn(cost, route);
-        if (DUMP) {
-            const float shuttle = __fmul_rn(__fmul_rn(__ll2float_rn((long long)ts.Sh.get(g)), c.dq_scale), 2.0f);
-            (void)shuttle;
+        if constexpr (DUMP) {
+            const float shuttle = __fmul_rn(__fmul_rn(__ll2float_rn(dSh[g]), c.dq_scale), 2.0f);
             if (o_nhu) o_nhu[g] = (int16_t)nhu;
             if (o_nsu) o_nsu[g] = (int16_t)nsu;
-            if (o_tc) o_tc[g] = ts.Tc.get(g);
-            if (o_tw) o_tw[g] = ts.Tw.get(g);
+            if (o_tc) o_tc[g] = dTc[g];
+            if (o_tw) o_tw[g] = dTw[g];
+            if (o_kf) o_kf[g] = kfv[g];
+            if (o_sh) o_sh[g] = dSh[g];
             if (o_tcost) o_tcost[g] = __fadd_rn(route, shuttle);
             if (o_hu) {
                 M r = hm;
@@ -1043,19 +1062,12 @@ __device__ bool stage_instance(const InstMeta &M, BlockShared &bs, unsigned char
         bs.base_cost = __int_as_float(0x7f800000);
         for (int g = 0; g < T && g < 16; ++g) bs.base_tc[g] = 0.f;
         if (bs.nbad == 0) {
+            // the base plan's T_compl, shuttle ratio N_SU / sum cap and exact shuttle sum of every active tour
             const MoveRec idm = {4, 0, 0, 0};
-            const ScoreOut r = score_candidate<SH, false>(c, p, idm, __int_as_float(0x7f800000), smem + sp.off_tour,
-                                                          tid, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr,
-                                                          nullptr);
-            TourState<SH> ts;
-            ts.bind(smem + sp.off_tour, tid);
-            for (int g = 0; g < T; ++g)
-                if (c.tour_cnt[g] > 0) {
-                    kf_base[g] = ts.KF.get(g);
-                    sh_base[g] = (long long)ts.Sh.get(g);
-                    if (g < 16) bs.base_tc[g] = ts.Tc.get(g);
-                }
-            bs.base_cost = r.cost;
+            bs.base_cost = score_candidate<SH, false, true>(c, p, idm, __int_as_float(0x7f800000), smem + sp.off_tour,
+                                                            tid, nullptr, nullptr, bs.base_tc, nullptr, nullptr,
+                                                            nullptr, nullptr, kf_base, sh_base)
+                               .cost;
         }
     }
     __syncthreads();
@@ -1744,6 +1756,25 @@ cudaError_t configure_kernels(int32_t shape, size_t smem)
     case SHAPE_T8_S64_DSMEM: return set_attrs<ShapeB>(smem);
     default: return set_attrs<ShapeC>(smem);
     }
+}
+
+// Resident blocks per SM of the search kernel with this much dynamic shared
+// memory (registers and shared memory both counted); 0 on error.
+int search_blocks_per_sm(int32_t shape, size_t smem)
+{
+    int n = 0;
+    cudaError_t e;
+    switch (shape) {
+    case SHAPE_T4_S64_DSMEM:
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, search_iteration_kernel<ShapeA>, ShapeA::NT, smem);
+        break;
+    case SHAPE_T8_S64_DSMEM:
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, search_iteration_kernel<ShapeB>, ShapeB::NT, smem);
+        break;
+    default:
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, search_iteration_kernel<ShapeC>, ShapeC::NT, smem);
+    }
+    return e == cudaSuccess ? n : 0;
 }
 
 cudaError_t launch_search_iteration(const LaunchCfg &cfg, const InstMeta *d_meta, const WorkItem *d_work,
