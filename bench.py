@@ -244,7 +244,8 @@ def main():
         else:
             from paper_1909_10286_gb300 import autotune
             tuned = autotune.tune(insts, n, base_params=kw)
-            params = biolog.make_params(n_cand=n, blocks_per_sm=tuned["blocks_per_sm"], tile=tuned["tile"], **kw)
+            params = biolog.make_params(n_cand=n, blocks_per_sm=tuned["blocks_per_sm"], tile=tuned["tile"],
+                                        lanes_per_cand=tuned.get("lanes_per_cand", 1), **kw)
     else:
         insts = [I.make_instance(args.workload, args.seed + rank)]
         params = biolog.make_params(n_cand=n, **kw)

@@ -95,6 +95,10 @@ typedef struct bl_params {
     int32_t blocks_per_sm;   /* 0 = autotuned; else resident blocks per SM to size the grid */
     int32_t tile;            /* 0 = autotuned; else candidates per work item */
     int32_t log_capacity;    /* iterations kept in the per-instance log (0 = 4096) */
+    int32_t lanes_per_cand;  /* 0 or 1: one thread scores a candidate; 4, 8, 16 or 32: a group
+                                of that many lanes of a warp scores it together, lane g holding
+                                tour g (>= the largest tour count; 4 or 8 for <= 4 tours, 8 or
+                                16 for <= 8, 16 or 32 above; else BL_EINVAL). Same results. */
     void *workspace;         /* device, optional: caller-owned buffer of
                                 bl_workspace_bytes() bytes, 256-byte aligned; NULL = the
                                 library allocates and frees its own */
@@ -294,9 +298,10 @@ int bl_features(bl_handle *h, int32_t inst, int32_t use_best, uint32_t iter, int
 int bl_search_step_learned(bl_handle *h, bl_mlp *mlp, int32_t n_iters, int32_t pool, int32_t n_keep, float rand_frac);
 
 /* Kernel configuration in use: threads per block, grid blocks, candidates
-   per work item, and the number of kernels one iteration launches. */
+   per work item, the number of kernels one iteration launches, and the lanes
+   that score one candidate (any pointer may be NULL). */
 int bl_get_config(bl_handle *h, int32_t *block_threads, int32_t *grid_blocks, int32_t *tile,
-                  int32_t *launches_per_iter);
+                  int32_t *launches_per_iter, int32_t *lanes_per_cand);
 
 /* Release everything the handle owns. */
 int bl_plan_free(bl_handle *h);

@@ -47,7 +47,8 @@ class bl_params(C.Structure):
     _fields_ = [("eps", C.c_float), ("p_swap", C.c_float), ("seed", C.c_uint64), ("inst_idx", C.c_uint32),
                 ("n_cand", C.c_int32), ("fix_field_bp", C.c_int32), ("fix_resources", C.c_int32),
                 ("gate", C.c_int32), ("block_threads", C.c_int32), ("blocks_per_sm", C.c_int32), ("tile", C.c_int32),
-                ("log_capacity", C.c_int32), ("workspace", C.c_void_p), ("workspace_bytes", C.c_size_t)]
+                ("log_capacity", C.c_int32), ("lanes_per_cand", C.c_int32), ("workspace", C.c_void_p),
+                ("workspace_bytes", C.c_size_t)]
 
 
 class bl_plan(C.Structure):
@@ -87,7 +88,7 @@ def load(path: str | None = None):
             L.bl_score_candidates.argtypes = [vp, C.c_int32, C.c_int32, C.c_uint32, C.c_float, C.c_int32, C.c_int32,
                                               vp, vp, vp, vp, vp]
             L.bl_decode_candidates.argtypes = [vp, C.c_int32, C.c_int32, C.c_uint32, vp, C.c_int32, vp]
-            L.bl_get_config.argtypes = [vp, vp, vp, vp, vp]
+            L.bl_get_config.argtypes = [vp, vp, vp, vp, vp, vp]
             L.bl_argmin_noalloc.argtypes = [vp, C.c_int32, C.c_int32, C.c_uint32, C.c_float, C.c_int32, C.c_int32,
                                             vp, vp]
             L.bl_features.argtypes = [vp, C.c_int32, C.c_int32, C.c_uint32, C.c_int32, C.c_int32, vp, vp]
@@ -125,10 +126,10 @@ class _InstanceArgs:
 
 def make_params(n_cand: int, eps: float = 0.5, seed: int = 0, inst_idx: int = 0, fix_field_bp: int = 0,
                 fix_resources: int = 0, gate: int = 1, p_swap: float = 0.0, block_threads: int = 0,
-                blocks_per_sm: int = 0, tile: int = 0, log_capacity: int = 0) -> bl_params:
+                blocks_per_sm: int = 0, tile: int = 0, log_capacity: int = 0, lanes_per_cand: int = 0) -> bl_params:
     return bl_params(float(eps), float(p_swap), int(seed), int(inst_idx), int(n_cand), int(fix_field_bp),
                      int(fix_resources), int(gate), int(block_threads), int(blocks_per_sm), int(tile),
-                     int(log_capacity), None, 0)
+                     int(log_capacity), int(lanes_per_cand), None, 0)
 
 
 def _check(rc: int, handle=None):
@@ -257,9 +258,10 @@ class Search:
         return self._stream
 
     def config(self) -> dict:
-        v = [C.c_int32() for _ in range(4)]
+        v = [C.c_int32() for _ in range(5)]
         _check(load().bl_get_config(self.h, *[C.byref(x) for x in v]), self.h)
-        return dict(block_threads=v[0].value, grid_blocks=v[1].value, tile=v[2].value, launches_per_iter=v[3].value)
+        return dict(block_threads=v[0].value, grid_blocks=v[1].value, tile=v[2].value, launches_per_iter=v[3].value,
+                    lanes_per_cand=v[4].value)
 
     def close(self):
         if getattr(self, "h", None):

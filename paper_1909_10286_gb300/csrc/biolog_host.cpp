@@ -431,7 +431,8 @@ int pick_shape(const std::vector<HostInst> &insts)
 void plan_work(bl_handle *h, int sms, int blocks_per_sm)
 {
     const int n = h->n_inst;
-    const int threads = h->cfg.threads;
+    // at least one candidate per thread, or per lane group of the cooperative kernel
+    const int threads = h->cfg.lanes > 1 ? kCoopThreads / h->cfg.lanes : h->cfg.threads;
     const int grid = sms * blocks_per_sm;
     long long total = (long long)n * h->prm.n_cand;
     int tile = h->prm.tile;
@@ -557,6 +558,13 @@ int init_common(const bl_instance *insts, int32_t n_inst, const bl_params *param
     h->cfg.threads = threads_of(shape);
     int maxT = 0;
     for (const HostInst &hi : h->insts) maxT = std::max(maxT, hi.T);
+    h->cfg.lanes = params->lanes_per_cand <= 1 ? 1 : params->lanes_per_cand;
+    if (h->cfg.lanes > 1 && (!coop_supported(shape, h->cfg.lanes) || h->cfg.lanes < maxT)) {
+        g_error = "lanes_per_cand " + std::to_string(h->cfg.lanes) + " is not built for this shape or is below the "
+                  "largest tour count " + std::to_string(maxT);
+        delete h;
+        return BL_EINVAL;
+    }
     for (const HostInst &hi : h->insts)
         if (hi.T > max_tours_of(shape) || hi.S > max_su_of(shape) || hi.H > (shape == SHAPE_T16_S128_GMEM ? 64 : max_su_of(shape))) {
             g_error = "no kernel shape fits";
@@ -589,7 +597,14 @@ int init_common(const bl_instance *insts, int32_t n_inst, const bl_params *param
         cudaError_t e = configure_kernels(shape, h->cfg.smem);
         if (e != cudaSuccess) { delete h; return cuda_fail(nullptr, e, "configure_kernels"); }
         // as many blocks per SM as registers and shared memory allow
-        bps = std::max(1, search_blocks_per_sm(shape, h->cfg.smem));
+        if (h->cfg.lanes > 1) {
+            const size_t csm = coop_shared_bytes(h->cfg);
+            e = configure_coop(shape, h->cfg.lanes, csm);
+            if (e != cudaSuccess) { delete h; return cuda_fail(nullptr, e, "configure_coop"); }
+            bps = std::max(1, coop_blocks_per_sm(shape, h->cfg.lanes, csm));
+        } else {
+            bps = std::max(1, search_blocks_per_sm(shape, h->cfg.smem));
+        }
         if (params->blocks_per_sm > 0) bps = params->blocks_per_sm;
     } else {
         bps = std::max(1, params->blocks_per_sm);
@@ -1023,10 +1038,12 @@ int bl_best_plan(bl_handle *h, int32_t inst, bl_plan *out)
     return BL_OK;
 }
 
-int bl_get_config(bl_handle *h, int32_t *block_threads, int32_t *grid_blocks, int32_t *tile, int32_t *launches_per_iter)
+int bl_get_config(bl_handle *h, int32_t *block_threads, int32_t *grid_blocks, int32_t *tile, int32_t *launches_per_iter,
+                  int32_t *lanes_per_cand)
 {
     if (!h) return BL_EINVAL;
-    if (block_threads) *block_threads = h->cfg.threads;
+    if (lanes_per_cand) *lanes_per_cand = h->cfg.lanes;
+    if (block_threads) *block_threads = h->cfg.lanes > 1 ? kCoopThreads : h->cfg.threads;
     if (grid_blocks) *grid_blocks = h->cfg.grid;
     if (tile) *tile = h->meta.empty() ? 0 : h->meta[0].tile;
     if (launches_per_iter) *launches_per_iter = 1;

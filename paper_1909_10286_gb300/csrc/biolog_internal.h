@@ -105,6 +105,7 @@ enum ShapeClass : int32_t {
 
 struct LaunchCfg {
     int32_t shape;
+    int32_t lanes;          // lanes per candidate of the search kernel (1: one thread per candidate)
     int32_t threads;        // threads per block
     int32_t grid;           // blocks
     size_t smem;            // dynamic shared memory bytes
@@ -140,6 +141,12 @@ size_t shared_bytes(int32_t shape, int32_t threads, int32_t max_prefix, int32_t 
                     int32_t max_B, int32_t max_T);
 cudaError_t configure_kernels(int32_t shape, size_t smem);
 int search_blocks_per_sm(int32_t shape, size_t smem);
+// cooperative search kernel (lanes per candidate > 1)
+constexpr int kCoopThreads = 256;
+bool coop_supported(int32_t shape, int32_t lanes);
+size_t coop_shared_bytes(const LaunchCfg &cfg);
+cudaError_t configure_coop(int32_t shape, int32_t lanes, size_t smem);
+int coop_blocks_per_sm(int32_t shape, int32_t lanes, size_t smem);
 int max_tours_of(int32_t shape);
 int threads_of(int32_t shape);
 int max_su_of(int32_t shape);

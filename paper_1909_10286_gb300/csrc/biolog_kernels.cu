@@ -924,10 +924,11 @@ struct BlockShared {
 };
 
 // Stage instance `inst` (tables by bulk copy, base plan, derived tables, base
-// tour aggregates). Returns false if the bounded wait gave up (error flag set).
+// per-BP and per-tour aggregates), without the base plan's own scoring.
+// Returns false if the bounded wait gave up (error flag set).
 template <class SH>
-__device__ bool stage_instance(const InstMeta &M, BlockShared &bs, unsigned char *smem, const SmemPlan &sp,
-                               const SearchParams &p, int use_best_override, uint32_t iter_override, Ctx &c)
+__device__ bool stage_base(const InstMeta &M, BlockShared &bs, unsigned char *smem, const SmemPlan &sp,
+                           const SearchParams &p, int use_best_override, uint32_t iter_override, Ctx &c)
 {
     const int tid = threadIdx.x, nt = blockDim.x;
     const uint32_t bytes = SH::DSM ? (uint32_t)M.L.total_bytes : (uint32_t)M.L.prefix_bytes;
@@ -1055,7 +1056,19 @@ __device__ bool stage_instance(const InstMeta &M, BlockShared &bs, unsigned char
         tLHU[g] = t.LHU; tLSU[g] = t.LSU; tA[g] = t.A; tDB2[g] = t.DB2;
     }
     __syncthreads();
-    // the base plan's own shuttle ratios and sums per tour, scored with the candidates' code
+    return true;
+}
+
+// stage_base, then the base plan's own per-tour T_compl, shuttle ratio and
+// shuttle sum, scored by thread 0 with the candidates' code.
+template <class SH>
+__device__ bool stage_instance(const InstMeta &M, BlockShared &bs, unsigned char *smem, const SmemPlan &sp,
+                               const SearchParams &p, int use_best_override, uint32_t iter_override, Ctx &c)
+{
+    if (!stage_base<SH>(M, bs, smem, sp, p, use_best_override, iter_override, c)) return false;
+    const int tid = threadIdx.x, T = M.T;
+    float *kf_base = const_cast<float *>(c.kf_base);
+    long long *sh_base = const_cast<long long *>(c.sh_base);
     if (tid == 0) {
         c.nbad = bs.nbad;
         for (int g = 0; g < T; ++g) { kf_base[g] = 0.f; sh_base[g] = 0; }
@@ -1103,6 +1116,95 @@ __device__ void write_plan(const Ctx &c, const MoveRec &m, int16_t *out)
 // ---------------------------------------------------------------------------
 // The search iteration kernel
 // ---------------------------------------------------------------------------
+// Block argmin of the work item's candidates (warp shuffle, then across
+// warps) into its slot; the last work item of the instance to finish takes the
+// argmin over the instance's slots and runs Steps 13-16 (replay the move,
+// update x_old, x*, C*, Tmax*, the log and the iteration counter).
+template <int NT>
+__device__ __forceinline__ void block_argmin_finalize(unsigned long long best, float best_t, BlockShared &bs,
+                                                      const InstMeta &M, const WorkItem &wi,
+                                                      unsigned long long *__restrict__ slot_key,
+                                                      float *__restrict__ slot_tmax,
+                                                      const int32_t *__restrict__ slot_base, const Ctx &c,
+                                                      const SearchParams &prm, uint32_t iter)
+{
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    // block argmin: warp shuffle, then across warps
+    for (int o = 16; o > 0; o >>= 1) {
+        const unsigned long long ok = __shfl_xor_sync(0xffffffffu, best, o);
+        const float ot = __shfl_xor_sync(0xffffffffu, best_t, o);
+        if (ok < best) { best = ok; best_t = ot; }
+    }
+    if (lane == 0) { bs.red[warp] = best; bs.redt[warp] = best_t; }
+    __syncthreads();
+    if (tid < 32) {
+        const int nw = NT >> 5;
+        best = (tid < nw) ? bs.red[tid] : ~0ull;
+        best_t = (tid < nw) ? bs.redt[tid] : 0.f;
+        for (int o = 16; o > 0; o >>= 1) {
+            const unsigned long long ok = __shfl_xor_sync(0xffffffffu, best, o);
+            const float ot = __shfl_xor_sync(0xffffffffu, best_t, o);
+            if (ok < best) { best = ok; best_t = ot; }
+        }
+        if (tid == 0) {
+            const int slot = slot_base[wi.inst] + wi.tile_idx;
+            slot_key[slot] = best;
+            slot_tmax[slot] = best_t;
+            __threadfence();
+            const uint32_t prev = atomicAdd(&M.state->done, 1u);
+            bs.last = (prev == (uint32_t)(M.n_tiles - 1)) ? 1 : 0;
+        }
+    }
+    __syncthreads();
+    if (bs.last) {
+        // Steps 13-16 for this instance: argmin over its work items
+        __threadfence();
+        if (tid < 32) {
+            unsigned long long bk = ~0ull;
+            float bt = 0.f;
+            const int s0 = slot_base[wi.inst];
+            for (int s = tid; s < M.n_tiles; s += 32) {
+                const unsigned long long k = __ldcg(&slot_key[s0 + s]);
+                const float t = __ldcg(&slot_tmax[s0 + s]);
+                if (k < bk) { bk = k; bt = t; }
+            }
+            for (int o = 16; o > 0; o >>= 1) {
+                const unsigned long long ok = __shfl_xor_sync(0xffffffffu, bk, o);
+                const float ot = __shfl_xor_sync(0xffffffffu, bt, o);
+                if (ok < bk) { bk = ok; bt = ot; }
+            }
+            if (tid == 0) {
+                const uint32_t istar = (uint32_t)(bk & 0xffffffffu);
+                const float cst = __uint_as_float((uint32_t)(bk >> 32));
+                InstState *st = M.state;
+                int ind = 0;
+                if (isfinite(cst)) {
+                    const MoveRec m = draw_move(c, prm, istar, iter, M.inst_idx);
+                    write_plan(c, m, M.xold);
+                    if (cst < st->cstar) {
+                        for (int k = 0; k < M.plan_len; ++k) M.xbest[k] = M.xold[k];
+                        st->cstar = cst;
+                        st->tmaxstar = bt;
+                        ind = (m.kind == 0 || m.kind == 2) ? 1 : 2;
+                    }
+                } else {
+                    const int16_t *pl = c.bp_order;
+                    for (int k = 0; k < M.plan_len; ++k) M.xold[k] = pl[k];
+                }
+                const int li = (int)(iter % (uint32_t)M.log_cap);
+                M.log_istar[li] = (int32_t)istar;
+                M.log_cistar[li] = cst;
+                M.log_usebest[li] = (int8_t)bs.use_best;
+                M.log_cstar[li] = st->cstar;
+                M.log_ind[li] = (int8_t)ind;
+                st->iter = iter + 1;
+                st->done = 0;
+            }
+        }
+    }
+    __syncthreads();
+}
+
 template <class SH>
 __global__ void __launch_bounds__(SH::NT, SH::MINB) search_iteration_kernel(const InstMeta *__restrict__ meta,
                                                                   const WorkItem *__restrict__ work, int32_t n_work,
@@ -1194,80 +1296,515 @@ __global__ void __launch_bounds__(SH::NT, SH::MINB) search_iteration_kernel(cons
                 qcount -= take;
             }
         }
-        // block argmin: warp shuffle, then across warps
-        for (int o = 16; o > 0; o >>= 1) {
-            const unsigned long long ok = __shfl_xor_sync(0xffffffffu, best, o);
-            const float ot = __shfl_xor_sync(0xffffffffu, best_t, o);
-            if (ok < best) { best = ok; best_t = ot; }
+        block_argmin_finalize<NT>(best, best_t, bs, M, wi, slot_key, slot_tmax, slot_base, c, prm, iter);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Cooperative scoring: L lanes per candidate, lane g holds tour g
+// ---------------------------------------------------------------------------
+// The same arithmetic as score_candidate, value for value, so a cooperative
+// search follows the same trajectory bit for bit. A group of L lanes (L >= the
+// number of tours, a power of two dividing 32) scores one candidate:
+//  - lane g keeps tour g's aggregates, unit sets and times in registers;
+//  - every local-minimisation round finds g_max, g_max2 and g_min by shuffle
+//    reductions (lowest tour index on ties, as the sequential scan), then tries
+//    up to L members of g_min at once: the first accepted in the sequential
+//    order (a ballot) is the one the sequential loop stops at;
+//  - the shuttle pass runs over the field positions, L at a time; its sums are
+//    exact integers, so their order does not matter;
+//  - the float cost is summed over the tours in index order, like the
+//    sequential sum.
+__device__ __forceinline__ int select_bit32(uint32_t w, int n)   // position of the n-th (0-based) set bit
+{
+    int pos = 0;
+#pragma unroll
+    for (int sh = 16; sh > 0; sh >>= 1) {
+        const uint32_t lo = w & ((1u << sh) - 1u);
+        const int cnt = __popc(lo);
+        if (n >= cnt) { n -= cnt; w >>= sh; pos += sh; }
+        else w = lo;
+    }
+    return pos;
+}
+__device__ __forceinline__ int select_bit64(unsigned long long w, int n)
+{
+    const uint32_t lo = (uint32_t)w;
+    const int cl = __popc(lo);
+    return n < cl ? select_bit32(lo, n) : 32 + select_bit32((uint32_t)(w >> 32), n - cl);
+}
+template <typename Mk>
+__device__ __forceinline__ int select_m(Mk w, int n)
+{
+    if constexpr (sizeof(Mk) == 4) return select_bit32((uint32_t)w, n);
+    else return select_bit64((unsigned long long)w, n);
+}
+// clear the lowest `n` set bits of a one- or two-word set (at least n + 1 are set)
+template <typename Mk>
+__device__ __forceinline__ void drop_lowest(Mk &w0, unsigned long long &w1, int n)
+{
+    const int c0 = popc_m(w0);
+    if (n >= c0) {
+        w0 = 0;
+        const int p = select_bit64(w1, n - c0 - 1 < 0 ? 0 : n - c0 - 1);
+        if (n > c0) w1 &= (p == 63) ? 0ull : (~0ull << (p + 1));
+    } else {
+        const int p = select_m(w0, n - 1);
+        constexpr int BITS = 8 * (int)sizeof(Mk);
+        w0 &= (p == BITS - 1) ? (Mk)0 : (Mk)(~(Mk)0 << (p + 1));
+    }
+}
+
+template <int L>
+__device__ __forceinline__ unsigned grp_ballot(unsigned gm, bool pred)
+{
+    const unsigned b = __ballot_sync(gm, pred);
+    const int base = (threadIdx.x & 31) & ~(L - 1);
+    return L == 32 ? b : ((b >> base) & ((1u << L) - 1u));
+}
+// (value, index) reductions over the group; invalid lanes carry +-inf and a large index
+template <int L>
+__device__ __forceinline__ void grp_argmax(float &x, int &i, unsigned gm)
+{
+#pragma unroll
+    for (int o = L / 2; o > 0; o >>= 1) {
+        const float ox = __shfl_xor_sync(gm, x, o, L);
+        const int oi = __shfl_xor_sync(gm, i, o, L);
+        if (ox > x || (ox == x && oi < i)) { x = ox; i = oi; }
+    }
+}
+template <int L>
+__device__ __forceinline__ void grp_argmin(float &x, int &i, unsigned gm)
+{
+#pragma unroll
+    for (int o = L / 2; o > 0; o >>= 1) {
+        const float ox = __shfl_xor_sync(gm, x, o, L);
+        const int oi = __shfl_xor_sync(gm, i, o, L);
+        if (ox < x || (ox == x && oi < i)) { x = ox; i = oi; }
+    }
+}
+template <int L>
+__device__ __forceinline__ float grp_max(float x, unsigned gm)
+{
+#pragma unroll
+    for (int o = L / 2; o > 0; o >>= 1) {
+        const float ox = __shfl_xor_sync(gm, x, o, L);
+        if (ox > x) x = ox;
+    }
+    return x;
+}
+template <int L>
+__device__ __forceinline__ long long grp_sum(long long v, unsigned gm)
+{
+#pragma unroll
+    for (int o = L / 2; o > 0; o >>= 1) v += __shfl_xor_sync(gm, v, o, L);
+    return v;
+}
+template <int L, typename V>
+__device__ __forceinline__ V grp_bcast(V v, int src, unsigned gm) { return __shfl_sync(gm, v, src, L); }
+
+constexpr int kNoTour = 1 << 20;
+
+// g_max, g_max2 and g_min of one local-minimisation round (Algorithm 2)
+template <int L>
+__device__ __forceinline__ void grp_picks(float t, bool act, int g, int na, unsigned gm, int &gx, float &tx, int &gx2,
+                                          float &tx2, int &gn, float &tn)
+{
+    tx = act ? t : -INFINITY;
+    gx = act ? g : kNoTour;
+    grp_argmax<L>(tx, gx, gm);
+    const bool c2 = act && g != gx;
+    tx2 = c2 ? t : -INFINITY;
+    gx2 = c2 ? g : kNoTour;
+    grp_argmax<L>(tx2, gx2, gm);
+    if (na == 2) { gn = gx2; tn = tx2; return; }
+    const bool c3 = c2 && g != gx2;
+    tn = c3 ? t : INFINITY;
+    gn = c3 ? g : kNoTour;
+    grp_argmin<L>(tn, gn, gm);
+}
+
+template <class SH, int L, bool IDENT>
+__device__ ScoreOut score_coop(const Ctx &c, const SearchParams &p, const MoveRec &m, float tmax_star, int lane,
+                               unsigned gm, float *o_tc, float *o_kf, long long *o_sh)
+{
+    constexpr int SW = SH::SW;
+    using M = typename SH::Mask;
+    using S = typename SH::Sum;
+    ScoreOut out;
+    View x;
+    x.set(c, m);
+    const unsigned touched = x.touched(c);
+    const int g = lane;   // this lane's tour
+    const int nb = g < c.T ? x.tour_len(c, g) : 0;
+    const bool act = nb > 0;
+    const unsigned amask = grp_ballot<L>(gm, act);
+    const int na = __popc(amask);
+    const int j = __popc(amask & ((1u << g) - 1u));   // rank among the active tours
+
+    // --- route aggregates (Fig. 1, Sec. 2.2)
+    long long lhu = 0, lsu = 0, ar = 0;
+    float db2 = 0.f;
+    if (act) {
+        if ((touched >> g) & 1u) {
+            const TourAgg t = tour_agg(c, x, g, nb);
+            lhu = t.LHU; lsu = t.LSU; ar = t.A; db2 = t.DB2;
+        } else {
+            lhu = c.tLHU[g]; lsu = c.tLSU[g]; ar = c.tA[g]; db2 = c.tDB2[g];
         }
-        if (lane == 0) { bs.red[warp] = best; bs.redt[warp] = best_t; }
-        __syncthreads();
-        if (tid < 32) {
-            const int nw = NT >> 5;
-            best = (tid < nw) ? bs.red[tid] : ~0ull;
-            best_t = (tid < nw) ? bs.redt[tid] : 0.f;
-            for (int o = 16; o > 0; o >>= 1) {
-                const unsigned long long ok = __shfl_xor_sync(0xffffffffu, best, o);
-                const float ot = __shfl_xor_sync(0xffffffffu, best_t, o);
-                if (ok < best) { best = ok; best_t = ot; }
+    }
+    const float LHU = __fmul_rn(__ll2float_rn(lhu), c.dq_scale);
+    const float LSU = __fmul_rn(__ll2float_rn(lsu), c.dq_scale);
+    const float A = __fmul_rn(__ll2float_rn(ar), c.aq_scale);
+    const float DB2 = db2;
+    const int di = (na - 1) * c.T;
+
+    // --- HU assignment (Sec. 2.5): round-robin dealing, then Algorithm 2 on T_compl
+    M Hm = 0;
+    S Rq = 0;
+    float tv = 0.f;
+    if (act) {
+        Hm = (M)c.hudeal_m[di + j];
+        Rq = (S)c.hudeal_q[di + j];
+        const float R = __fmul_rn(to_f(Rq), c.rqs);
+        tv = __fmaf_rn(LHU, c.inv_v, __fdividef(A, R));
+    }
+    if (!p.fix_resources && na >= 2) {
+        for (int round = 0; round < c.H; ++round) {
+            int gx, gx2, gn;
+            float tx, tx2, tn;
+            grp_picks<L>(tv, act, g, na, gm, gx, tx, gx2, tx2, gn, tn);
+            const M mn = grp_bcast<L>(Hm, gn, gm);
+            if (popc_m(mn) <= 1) break;
+            const int last = hibit_m(mn);
+            const float Lx = grp_bcast<L>(LHU, gx, gm), Ax = grp_bcast<L>(A, gx, gm);
+            const float Ln = grp_bcast<L>(LHU, gn, gm), An = grp_bcast<L>(A, gn, gm);
+            const S rqx = grp_bcast<L>(Rq, gx, gm), rqn = grp_bcast<L>(Rq, gn, gm);
+            M rem = mn;
+            unsigned long long rem1 = 0ull;
+            int k;
+            float tmx, tmn;
+            S nqx, nqn;
+            while (true) {
+                const int cnt = popc_m(rem);
+                bool cond = false;
+                int kk = 0;
+                float a_tmx = 0.f, a_tmn = 0.f;
+                S a_nqx = 0, a_nqn = 0;
+                if (lane < cnt) {
+                    kk = select_m(rem, lane);
+                    a_nqx = rqx + (S)c.hurq[kk];
+                    a_nqn = rqn - (S)c.hurq[kk];
+                    a_tmx = __fmaf_rn(Lx, c.inv_v, __fdividef(Ax, __fmul_rn(to_f(a_nqx), c.rqs)));
+                    a_tmn = __fmaf_rn(Ln, c.inv_v, __fdividef(An, __fmul_rn(to_f(a_nqn), c.rqs)));
+                    const float ref = (na == 2) ? a_tmn : tx2;
+                    cond = (a_tmx < ref) || (kk == last);
+                }
+                const unsigned bal = grp_ballot<L>(gm, cond);
+                if (bal) {
+                    const int w = __ffs(bal) - 1;
+                    k = grp_bcast<L>(kk, w, gm);
+                    tmx = grp_bcast<L>(a_tmx, w, gm);
+                    tmn = grp_bcast<L>(a_tmn, w, gm);
+                    nqx = grp_bcast<L>(a_nqx, w, gm);
+                    nqn = grp_bcast<L>(a_nqn, w, gm);
+                    break;
+                }
+                drop_lowest(rem, rem1, L);   // none of these L accepted (the last member always is)
             }
-            if (tid == 0) {
-                const int slot = slot_base[wi.inst] + wi.tile_idx;
-                slot_key[slot] = best;
-                slot_tmax[slot] = best_t;
-                __threadfence();
-                const uint32_t prev = atomicAdd(&M.state->done, 1u);
-                bs.last = (prev == (uint32_t)(M.n_tiles - 1)) ? 1 : 0;
-            }
+            float nm = (tmx > tmn) ? tmx : tmn;
+            const float other = grp_max<L>((act && g != gx && g != gn) ? tv : -INFINITY, gm);
+            if (other > nm) nm = other;
+            if (!(nm < tx)) break;   // the accepted move does not lower the maximum: keep the old state
+            const M bit = (M)1 << k;
+            if (g == gx) { Hm |= bit; Rq = nqx; tv = tmx; }
+            if (g == gn) { Hm &= ~bit; Rq = nqn; tv = tmn; }
         }
-        __syncthreads();
-        if (bs.last) {
-            // Steps 13-16 for this instance: argmin over its work items
-            __threadfence();
-            if (tid < 32) {
-                unsigned long long bk = ~0ull;
-                float bt = 0.f;
-                const int s0 = slot_base[wi.inst];
-                for (int s = tid; s < M.n_tiles; s += 32) {
-                    const unsigned long long k = __ldcg(&slot_key[s0 + s]);
-                    const float t = __ldcg(&slot_tmax[s0 + s]);
-                    if (k < bk) { bk = k; bt = t; }
-                }
-                for (int o = 16; o > 0; o >>= 1) {
-                    const unsigned long long ok = __shfl_xor_sync(0xffffffffu, bk, o);
-                    const float ot = __shfl_xor_sync(0xffffffffu, bt, o);
-                    if (ok < bk) { bk = ok; bt = ot; }
-                }
-                if (tid == 0) {
-                    const uint32_t istar = (uint32_t)(bk & 0xffffffffu);
-                    const float cst = __uint_as_float((uint32_t)(bk >> 32));
-                    InstState *st = M.state;
-                    int ind = 0;
-                    if (isfinite(cst)) {
-                        const MoveRec m = draw_move(c, prm, istar, iter, M.inst_idx);
-                        write_plan(c, m, M.xold);
-                        if (cst < st->cstar) {
-                            for (int k = 0; k < M.plan_len; ++k) M.xbest[k] = M.xold[k];
-                            st->cstar = cst;
-                            st->tmaxstar = bt;
-                            ind = (m.kind == 0 || m.kind == 2) ? 1 : 2;
-                        }
+    }
+    const float tmax = grp_max<L>(act ? tv : -INFINITY, gm);
+    if (IDENT && act) o_tc[g] = tv;
+
+    // --- SU assignment (Algorithm 2, Eq. 6); R(g) is fixed now
+    M S0 = 0;
+    unsigned long long S1 = 0ull;
+    S Saq = 0;
+    float iR = 0.f, tw = 0.f;
+    int star = 0;
+    if (act) {
+        S0 = (M)c.sudeal_m[(di + j) * 2];
+        if (SW > 1) S1 = c.sudeal_m[(di + j) * 2 + 1];
+        Saq = (S)c.sudeal_q[di + j];
+        iR = __fdividef(1.0f, __fmul_rn(to_f(Rq), c.rqs));
+        star = su_star<SH>(c, S0, S1);
+        const float fill = __fmul_rn(to_f((S)(Saq - (S)c.sufq[star])), c.fqs);
+        tw = __fmaf_rn(-fill, iR, __fmul_rn(DB2, c.suinv[star]));
+    }
+    if (!p.fix_resources && na >= 2) {
+        for (int round = 0; round < c.S; ++round) {
+            int gx, gx2, gn;
+            float tx, tx2, tn;
+            grp_picks<L>(tw, act, g, na, gm, gx, tx, gx2, tx2, gn, tn);
+            const M n0 = grp_bcast<L>(S0, gn, gm);
+            const unsigned long long n1 = (SW > 1) ? grp_bcast<L>(S1, gn, gm) : 0ull;
+            if (popc_m(n0) + (SW > 1 ? popc_m(n1) : 0) <= 1) break;
+            const int last = (SW > 1 && n1) ? 64 + hibit_m(n1) : hibit_m(n0);
+            const int star_x = grp_bcast<L>(star, gx, gm), grp_x = c.sugrp[star_x];
+            const int star_n = grp_bcast<L>(star, gn, gm);
+            const S sqx = grp_bcast<L>(Saq, gx, gm), sqn = grp_bcast<L>(Saq, gn, gm);
+            const float DBx = grp_bcast<L>(DB2, gx, gm), DBn = grp_bcast<L>(DB2, gn, gm);
+            const float iRx = grp_bcast<L>(iR, gx, gm), iRn = grp_bcast<L>(iR, gn, gm);
+            M r0 = n0;
+            unsigned long long r1 = n1;
+            int k, sx, sn;
+            float tmx, tmn;
+            while (true) {
+                const int c0 = popc_m(r0);
+                const int cnt = c0 + (SW > 1 ? popc_m(r1) : 0);
+                bool cond = false;
+                int kk = 0, a_sx = 0, a_sn = 0;
+                float a_tmx = 0.f, a_tmn = 0.f;
+                if (lane < cnt) {
+                    kk = lane < c0 ? select_m(r0, lane) : 64 + select_bit64(r1, lane - c0);
+                    const float ak = c.sufill[kk];
+                    const int gk = c.sugrp[kk];
+                    if (gk > grp_x || (gk == grp_x && kk < star_x)) {
+                        a_sx = kk;
+                        a_tmx = __fmaf_rn(-__fmul_rn(to_f(sqx), c.fqs), iRx, __fmul_rn(DBx, c.suinv[kk]));
                     } else {
-                        const int16_t *pl = c.bp_order;
-                        for (int k = 0; k < M.plan_len; ++k) M.xold[k] = pl[k];
+                        a_sx = star_x;
+                        a_tmx = __fmaf_rn(-ak, iRx, tx);
                     }
-                    const int li = (int)(iter % (uint32_t)M.log_cap);
-                    M.log_istar[li] = (int32_t)istar;
-                    M.log_cistar[li] = cst;
-                    M.log_usebest[li] = (int8_t)bs.use_best;
-                    M.log_cstar[li] = st->cstar;
-                    M.log_ind[li] = (int8_t)ind;
-                    st->iter = iter + 1;
-                    st->done = 0;
+                    if (kk != star_n) {
+                        a_sn = star_n;
+                        a_tmn = __fmaf_rn(ak, iRn, tn);
+                    } else {
+                        M b0 = n0;
+                        unsigned long long b1 = n1;
+                        if (kk < 64) b0 &= ~((M)1 << kk); else b1 &= ~(1ull << (kk - 64));
+                        a_sn = su_star<SH>(c, b0, b1);
+                        a_tmn = __fmaf_rn(-__fmul_rn(to_f((S)(sqn - (S)c.sufq[kk] - (S)c.sufq[a_sn])), c.fqs), iRn,
+                                          __fmul_rn(DBn, c.suinv[a_sn]));
+                    }
+                    const float ref = (na == 2) ? a_tmn : tx2;
+                    cond = (a_tmx < ref) || (kk == last);
+                }
+                const unsigned bal = grp_ballot<L>(gm, cond);
+                if (bal) {
+                    const int w = __ffs(bal) - 1;
+                    k = grp_bcast<L>(kk, w, gm);
+                    sx = grp_bcast<L>(a_sx, w, gm);
+                    sn = grp_bcast<L>(a_sn, w, gm);
+                    tmx = grp_bcast<L>(a_tmx, w, gm);
+                    tmn = grp_bcast<L>(a_tmn, w, gm);
+                    break;
+                }
+                drop_lowest(r0, r1, L);
+            }
+            float nm = (tmx > tmn) ? tmx : tmn;
+            const float other = grp_max<L>((act && g != gx && g != gn) ? tw : -INFINITY, gm);
+            if (other > nm) nm = other;
+            if (!(nm < tx)) break;
+            if (g == gx) {
+                if (k < 64) S0 |= (M)1 << k; else S1 |= 1ull << (k - 64);
+                Saq = (S)(sqx + (S)c.sufq[k]);
+                star = sx;
+                tw = tmx;
+            }
+            if (g == gn) {
+                if (k < 64) S0 &= ~((M)1 << k); else S1 &= ~(1ull << (k - 64));
+                Saq = (S)(sqn - (S)c.sufq[k]);
+                star = sn;
+                tw = tmn;
+            }
+        }
+    }
+
+    // --- path-length cost (Sec. 2.2, Eq. 4): exact shuttle sums in fixed point
+    int nsu = 0;
+    float kf = 0.f;
+    double capd = 0.0;
+    if (act) {
+        nsu = popc_m(S0) + (SW > 1 ? popc_m(S1) : 0);
+        const long long cs = cap_sum<SH>(c, S0, S1);
+        kf = __fdividef((float)nsu, __fmul_rn(__ll2float_rn(cs), c.cqs));
+        capd = (double)cs * c.cqs_d;
+        if (IDENT) o_kf[g] = kf;
+    }
+    unsigned moved = 0u;   // tours whose field -> BP content changed
+    if (x.kind == 0 && x.sg != x.dg) moved = (1u << c.bp_tour[x.sg]) | (1u << c.bp_tour[x.dg]);
+    else if (x.kind == 1 && x.sg != x.dg) moved = (1u << x.sg) | (1u << x.dg);
+    else if (x.kind == 2 && c.field_bp[x.v] != c.field_bp[x.w])
+        moved = (1u << c.bp_tour[c.field_bp[x.v]]) | (1u << c.bp_tour[c.field_bp[x.w]]);
+    else if (x.kind == 3 && c.bp_tour[x.v] != c.bp_tour[x.w]) moved = (1u << c.bp_tour[x.v]) | (1u << c.bp_tour[x.w]);
+    const bool fr = act && (!c.memo || ((moved >> g) & 1u) || kf != c.kf_base[g]);
+    const unsigned fresh = grp_ballot<L>(gm, fr);
+    long long acc = (act && !fr) ? c.sh_base[g] : 0ll;
+    if (IDENT && act) o_sh[g] = 0;
+    if (IDENT) __syncwarp(gm);
+    // Eq. 4 for a field of tour t: FP32 fast path, the exact test near an integer
+    auto ceil_fast = [&](float sup, float kft, bool &amb) -> int {
+        const float q = __fmul_rn(sup, kft);
+        const float rq = rintf(q);
+        amb = !(fabsf(q - rq) > q * (1.0f / 2097152.0f));
+        return (int)ceilf(q);
+    };
+    if (fresh) {
+        for (int k0 = 0; k0 < c.F; k0 += L) {
+            const int kk = k0 + lane;
+            int t = -1;
+            float sup = 0.f;
+            int dq = 0;
+            if (kk < c.F) {
+                const int f = c.field_order[kk];
+                const int b = c.field_bp[f];   // base BP of this position
+                if (x.bp_of_field(c, f) == b) {   // moved fields are added below
+                    const int tb = x.tour_of_bp(c, b);
+                    if ((fresh >> tb) & 1u) { t = tb; sup = c.supply[f]; dq = c.dqown[kk]; }
+                }
+            }
+            const int src = t < 0 ? 0 : t;
+            const float kft = grp_bcast<L>(kf, src, gm);
+            bool amb = false;
+            int n = 0;
+            if (t >= 0) n = ceil_fast(sup, kft, amb);
+            if (grp_ballot<L>(gm, amb)) {   // rare: the tour's exact capacity sum decides
+                const int nst = grp_bcast<L>(nsu, src, gm);
+                const double cdt = grp_bcast<L>(capd, src, gm);
+                if (amb) n = exact_ceil(sup, nst, cdt, __fmul_rn(sup, kft));
+            }
+            if (t >= 0) {
+                const long long a = (long long)n * (long long)dq;
+                acc += a;
+                if (IDENT) atomicAdd((unsigned long long *)&o_sh[t], (unsigned long long)a);
+            }
+        }
+        int mv_f0 = -1, mv_f1 = -1;
+        if (x.kind == 0 && x.sg != x.dg) mv_f0 = x.v;
+        if (x.kind == 2 && c.field_bp[x.v] != c.field_bp[x.w]) { mv_f0 = x.v; mv_f1 = x.w; }
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+            const int f = q == 0 ? mv_f0 : mv_f1;
+            if (f >= 0) {   // uniform over the group
+                const int b = x.bp_of_field(c, f);
+                const int t = x.tour_of_bp(c, b);
+                const float kft = grp_bcast<L>(kf, t, gm);
+                const int nst = grp_bcast<L>(nsu, t, gm);
+                const double cdt = grp_bcast<L>(capd, t, gm);
+                bool amb;
+                int n = ceil_fast(c.supply[f], kft, amb);
+                if (amb) n = exact_ceil(c.supply[f], nst, cdt, __fmul_rn(c.supply[f], kft));
+                if (lane == 0) {
+                    const long long a = (long long)n * c.dq(1 + c.B + f, 1 + b);
+                    acc += a;
+                    if (IDENT) atomicAdd((unsigned long long *)&o_sh[t], (unsigned long long)a);
                 }
             }
         }
-        __syncthreads();
+    }
+    const long long shq = grp_sum<L>(acc, gm);
+    // cost: tours in index order, as the sequential sum
+    const float route = act ? __fadd_rn(__fmul_rn((float)popc_m(Hm), LHU), __fmul_rn((float)nsu, LSU)) : 0.f;
+    float cost = 0.f;
+    for (int t = 0; t < c.T; ++t) {
+        const float r = grp_bcast<L>(route, t, gm);
+        if ((amask >> t) & 1u) cost = __fadd_rn(cost, r);
+    }
+    cost = __fadd_rn(cost, __fmul_rn(__fmul_rn(__ll2float_rn(shq), c.dq_scale), 2.0f));
+    // --- completion-time gate (Sec. 2.5)
+    if ((p.gate == 1 && tmax > tmax_star) || (p.gate == 2 && tmax >= tmax_star)) cost = __int_as_float(0x7f800000);
+    out.cost = cost;
+    out.tmax = tmax;
+    return out;
+}
+
+constexpr int COOP_NT = 256;   // threads per block of the cooperative kernel
+
+// stage_base, then the base plan's own per-tour report scored by the first group
+template <class SH, int L>
+__device__ bool stage_coop(const InstMeta &M, BlockShared &bs, unsigned char *smem, const SmemPlan &sp,
+                           const SearchParams &p, Ctx &c)
+{
+    if (!stage_base<SH>(M, bs, smem, sp, p, -1, 0xffffffffu, c)) return false;
+    const int tid = threadIdx.x;
+    if (tid < L) {
+        const unsigned gm = L == 32 ? 0xffffffffu : ((1u << L) - 1u);
+        float *kf_base = const_cast<float *>(c.kf_base);
+        long long *sh_base = const_cast<long long *>(c.sh_base);
+        c.nbad = bs.nbad;
+        if (tid < M.T) { kf_base[tid] = 0.f; sh_base[tid] = 0; }
+        if (tid < 16) bs.base_tc[tid] = 0.f;
+        __syncwarp(gm);
+        float cost = __int_as_float(0x7f800000);
+        if (bs.nbad == 0) {
+            const MoveRec idm = {4, 0, 0, 0};
+            cost = score_coop<SH, L, true>(c, p, idm, __int_as_float(0x7f800000), tid, gm, bs.base_tc, kf_base,
+                                           sh_base)
+                       .cost;
+        }
+        if (tid == 0) bs.base_cost = cost;
+    }
+    __syncthreads();
+    c.nbad = bs.nbad;
+    c.memo = 1;
+    return true;
+}
+
+// One iteration of Algorithm 1 with L lanes per candidate: the work
+// decomposition, list mode, argmin slots and Steps 13-16 of the one-thread
+// kernel; each group of L lanes draws and scores candidates of the tile in turn.
+template <class SH, int L>
+__global__ void __launch_bounds__(COOP_NT) search_iteration_coop_kernel(
+    const InstMeta *__restrict__ meta, const WorkItem *__restrict__ work, int32_t n_work, SearchParams prm, SmemPlan sp,
+    unsigned long long *__restrict__ slot_key, float *__restrict__ slot_tmax, const int32_t *__restrict__ slot_base,
+    const uint32_t *__restrict__ cand_list, const int32_t *__restrict__ cand_count, int32_t list_stride)
+{
+    static_assert(L >= SH::MAXT && L <= 32 && (32 % L) == 0, "one lane per tour, groups inside a warp");
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ BlockShared bs;
+    const int tid = threadIdx.x;
+    const int gl = tid & (L - 1), grp = tid / L;
+    constexpr int NG = COOP_NT / L;
+    const unsigned gm = L == 32 ? 0xffffffffu : (((1u << L) - 1u) << ((tid & 31) & ~(L - 1)));
+    if (tid == 0) {
+        mbar_init(&bs.mbar, 1);
+        fence_mbar_init();
+        bs.phase = 0;
+        bs.staged = -1;
+    }
+    __syncthreads();
+    Ctx c;
+    for (int w = blockIdx.x; w < n_work; w += gridDim.x) {
+        const WorkItem wi = work[w];
+        const InstMeta &M = meta[wi.inst];
+        if (bs.staged != wi.inst) {
+            if (!stage_coop<SH, L>(M, bs, smem, sp, prm, c)) return;
+            if (tid == 0) bs.staged = wi.inst;
+            __syncthreads();
+        }
+        const float tmax_star = M.state->tmaxstar;
+        const uint32_t iter = bs.iter;
+        const int list_n = cand_list ? cand_count[wi.inst] : 0;
+        const uint32_t *ilist = cand_list ? cand_list + (size_t)wi.inst * list_stride : nullptr;
+        const int tl = cand_list ? max(32, ((min(M.n_cand, list_n) + M.n_tiles - 1) / M.n_tiles + 31) & ~31) : M.tile;
+        const int c0 = wi.tile_idx * tl;
+        const int c1 = min(c0 + tl, cand_list ? min(M.n_cand, list_n) : M.n_cand);
+        unsigned long long best = ~0ull;
+        float best_t = 0.f;
+        for (int pos = c0 + grp; pos < c1; pos += NG) {
+            const int i = ilist ? (int)ilist[pos] : pos;
+            const MoveRec m = draw_move(c, prm, (uint32_t)i, iter, M.inst_idx);
+            unsigned long long k;
+            float t = __int_as_float(0x7f800000);
+            if (demand_ok(c, m)) {
+                const ScoreOut r = score_coop<SH, L, false>(c, prm, m, tmax_star, gl, gm, nullptr, nullptr, nullptr);
+                k = make_key(r.cost, (uint32_t)i);
+                t = r.tmax;
+            } else {
+                k = make_key(__int_as_float(0x7f800000), (uint32_t)i);
+            }
+            if (k < best) { best = k; best_t = t; }
+        }
+        block_argmin_finalize<COOP_NT>(best, best_t, bs, M, wi, slot_key, slot_tmax, slot_base, c, prm, iter);
     }
 }
 
@@ -1729,6 +2266,60 @@ static SmemPlan plan_for(const LaunchCfg &cfg)
     }
 }
 
+// the cooperative kernel keeps tour state in registers and needs no queues
+static SmemPlan coop_plan_for(const LaunchCfg &cfg)
+{
+    return carve(0, 0, cfg.max_prefix, cfg.max_plan_len, cfg.max_F, cfg.max_B, cfg.max_T);
+}
+
+size_t coop_shared_bytes(const LaunchCfg &cfg) { return coop_plan_for(cfg).total; }
+
+// Calls f with the cooperative kernel instance for (shape, lanes), or returns
+// cudaErrorInvalidValue if that pair is not built.
+template <class F>
+static cudaError_t with_coop_kernel(int32_t shape, int32_t lanes, F &&f)
+{
+    switch (shape) {
+    case SHAPE_T4_S64_DSMEM:
+        if (lanes == 4) return f(search_iteration_coop_kernel<ShapeA, 4>);
+        if (lanes == 8) return f(search_iteration_coop_kernel<ShapeA, 8>);
+        break;
+    case SHAPE_T8_S64_DSMEM:
+        if (lanes == 8) return f(search_iteration_coop_kernel<ShapeB, 8>);
+        if (lanes == 16) return f(search_iteration_coop_kernel<ShapeB, 16>);
+        break;
+    default:
+        if (lanes == 16) return f(search_iteration_coop_kernel<ShapeC, 16>);
+        if (lanes == 32) return f(search_iteration_coop_kernel<ShapeC, 32>);
+    }
+    return cudaErrorInvalidValue;
+}
+
+bool coop_supported(int32_t shape, int32_t lanes)
+{
+    switch (shape) {
+    case SHAPE_T4_S64_DSMEM: return lanes == 4 || lanes == 8;
+    case SHAPE_T8_S64_DSMEM: return lanes == 8 || lanes == 16;
+    default: return lanes == 16 || lanes == 32;
+    }
+}
+
+cudaError_t configure_coop(int32_t shape, int32_t lanes, size_t smem)
+{
+    return with_coop_kernel(shape, lanes, [&](auto kern) {
+        return cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    });
+}
+
+int coop_blocks_per_sm(int32_t shape, int32_t lanes, size_t smem)
+{
+    int n = 0;
+    const cudaError_t e = with_coop_kernel(shape, lanes, [&](auto kern) {
+        return cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kern, COOP_NT, smem);
+    });
+    return e == cudaSuccess ? n : 0;
+}
+
 size_t shared_bytes(int32_t shape, int32_t threads, int32_t max_prefix, int32_t max_plan_len, int32_t max_F,
                     int32_t max_B, int32_t max_T)
 {
@@ -1782,6 +2373,16 @@ cudaError_t launch_search_iteration(const LaunchCfg &cfg, const InstMeta *d_meta
                                     const int32_t *slot_base, cudaStream_t s, const uint32_t *cand_list,
                                     const int32_t *cand_count, int32_t list_stride)
 {
+    if (cfg.lanes > 1) {
+        const SmemPlan cp = coop_plan_for(cfg);
+        const cudaError_t e = with_coop_kernel(cfg.shape, cfg.lanes, [&](auto kern) {
+            kern<<<cfg.grid, COOP_NT, cp.total, s>>>(d_meta, d_work, n_work, prm, cp, slot_key, slot_tmax, slot_base,
+                                                     cand_list, cand_count, list_stride);
+            return cudaSuccess;
+        });
+        if (e != cudaSuccess) return e;
+        return cudaGetLastError();
+    }
     const SmemPlan sp = plan_for(cfg);
     switch (cfg.shape) {
     case SHAPE_T4_S64_DSMEM:
