@@ -158,6 +158,100 @@ def oracle_throughput(inst, params_kw, n_cand, budget_s, threads, max_iters=50, 
     return m * iters / dt, m, iters, threads
 
 
+WORKLOAD_LEARNED = ("learned proposals on the paper-scale instance: per iteration 2^20 Philox moves featurised and "
+                    "ranked by the MLP 64-256-256-256-1 (BF16, tensor cores), the 0.9*2^18 best plus ~10% random "
+                    "moves scored exactly")
+
+
+def run_learned(args, ws, rank, local):
+    """Config-4 form: ranked proposals. value = exactly scored candidates/s; the
+    roofline is the fused MLP forward's (the dominant kernel), timed on its own
+    with CUDA events on the same pool of features."""
+    import numpy as np
+    import torch
+
+    from paper_1909_10286_gb300 import biolog, learned
+    from paper_1909_10286_gb300 import instances as I
+
+    torch.cuda.set_device(local)
+    pool, keep = 1 << 20, int(0.9 * (1 << 18))
+    rand_frac = 0.1 * (1 << 18) / (pool - keep)
+    t0 = time.time()
+    X, T = learned.collect(I.make_batch("paper", range(100 + 10 * rank, 104 + 10 * rank)), iters=12, sample=8192)
+    net0, losses = learned.train(X, T, hidden=256, steps=600, batch=4096, lr=1e-3, max_batch=8192)
+    t_train = time.time() - t0
+    inst = I.make_instance("paper", args.seed + rank)
+    S = biolog.Search([inst], biolog.make_params(n_cand=pool, eps=0.5, seed=1000 + args.seed + rank, gate=1))
+    net = net0.copy(stream=S.stream, max_batch=pool)
+    net0.close()
+    stream = S.stream
+    S.search_step_learned(net, args.warmup, pool, keep, rand_frac)
+    torch.cuda.synchronize()
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    clocks = ClockSampler(local)
+    clocks.start()
+    _barrier(ws)
+    torch.cuda.synchronize()
+    for a, b in evs:
+        with torch.cuda.stream(stream):
+            flush.zero_()
+        a.record(stream)
+        S.search_step_learned(net, 1, pool, keep, rand_frac)
+        b.record(stream)
+    torch.cuda.synchronize()
+    _barrier(ws)
+    clk = clocks.stop()
+    t_ms = _max_over_ranks(sum(a.elapsed_time(b) for a, b in evs), ws)
+    ms_step = t_ms / args.steps
+    # exactly scored candidates per iteration: the kept list (its length is data dependent)
+    feat = torch.empty((pool, 64), dtype=torch.bfloat16, device="cuda")
+    st = S.get_state()
+    S.features(-1, 0xFFFFFFFF, 0, pool, feat)
+    y = torch.empty(pool, dtype=torch.float32, device="cuda")
+    with torch.cuda.stream(stream):
+        net.forward(feat, y)
+    torch.cuda.synchronize()
+    yv = y.cpu().numpy()
+    sample = np.sort(yv[(np.arange(4096) * pool) // 4096])
+    th = sample[min(4095, keep * 4096 // pool)]
+    n_exact = int((yv <= th).sum()) + int(round(rand_frac * int((yv > th).sum())))
+    value = n_exact * args.steps * ws / (t_ms / 1e3)
+    # the fused MLP forward alone, on the same features, timed with CUDA events on its stream
+    fe = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(5)]
+    for a, b in fe:
+        with torch.cuda.stream(stream):
+            flush.zero_()
+        a.record(stream)
+        net.forward(feat, y)
+        b.record(stream)
+    torch.cuda.synchronize()
+    ms_mlp = statistics.median(a.elapsed_time(b) for a, b in fe)
+    flop = 2.0 * (64 * 256 + 2 * 256 * 256 + 256) * pool
+    peaks = _peaks()
+    peak = float(peaks.get("bf16_tflops", 1900.0))
+    achieved = flop / (ms_mlp / 1e3) / 1e12
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32 scorer, bf16 ranker", "data": "synthetic",
+            "config": {"workload": WORKLOAD_LEARNED, "instance_seed": args.seed, "pool": pool, "keep": keep,
+                       "rand_frac": rand_frac, "exact_per_iter": n_exact,
+                       "l2": "flushed before every timed step (256 MiB device write)",
+                       "ranker_training": {"tuples": int(X.shape[0]), "steps": 600, "s": round(t_train, 1)},
+                       "kernel": S.config(), "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU"},
+            "proposals_per_s": pool * args.steps * ws / (t_ms / 1e3),
+            "gpu_launches": args.steps * 5, "clocks": clk,
+            "e2e": {"value": None, "note": "the end-to-end number is on the default paper line"},
+            "roofline": {"bound": "tensor", "kernel": "fused_mlp_forward_kernel", "achieved": achieved, "peak": peak,
+                         "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None, "ms_per_launch": ms_mlp,
+                         "flop_per_launch": flop,
+                         "peak_basis": "bf16_tflops (burst) of MEASURED_PEAKS.json; kernel timed alone"}}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    net.close()
+    S.close()
+
+
 def run_reference(args, ws, rank):
     if rank != 0:
         return
@@ -214,6 +308,9 @@ def main():
     ws, rank, local = _dist()
     if args.impl == "reference":
         run_reference(args, ws, rank)
+        return
+    if args.workload == "learned":
+        run_learned(args, ws, rank, local)
         return
     if args.study:
         import torch
