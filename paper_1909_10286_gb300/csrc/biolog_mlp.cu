@@ -253,7 +253,43 @@ gemm_bf16_tn_kernel(const __nv_bfloat16 *__restrict__ A, const __nv_bfloat16 *__
 //                                                      -> LBO H * 16, SBO 128
 // Warp w (8 warps) reads TMEM lanes 32 (w % 4) .. +31 and the column half w / 4.
 constexpr int FTHREADS = 256;
-constexpr int FKC = 64;   // K per weight chunk
+constexpr int FKMAX = 64;   // largest K per weight chunk
+
+// Weight chunking: a bulk copy costs about the same time whatever its size up
+// to at least 64 KB, so chunks are as wide in K as shared memory allows next to
+// two tiles' activations: K1 per chunk for layer 1 and K2 for layers 2 and 3
+// (multiples of 16, at most 64; a chunk is H x K BF16, 32 KB at H = 256).
+// Chunk order: the layer-1 chunks, then layer 2's, then layer 3's.
+struct FusedGeom {
+    int k1, k2, nch1, nch2, cpt;
+    int xkb, hkb;          // 8-element K blocks of the X and H operand layouts
+    int max_chunk_bytes;
+};
+
+__host__ __device__ inline FusedGeom fused_geom(int I, int H)
+{
+    FusedGeom g;
+    const int i16 = (I + 15) & ~15;
+    g.k1 = i16 < FKMAX ? i16 : FKMAX;
+    g.nch1 = (i16 + g.k1 - 1) / g.k1;
+    g.k2 = H < FKMAX ? H : FKMAX;
+    g.nch2 = (H + g.k2 - 1) / g.k2;
+    g.cpt = g.nch1 + 2 * g.nch2;
+    g.xkb = g.nch1 * g.k1 / 8;
+    g.hkb = g.nch2 * g.k2 / 8;
+    g.max_chunk_bytes = H * (g.k1 > g.k2 ? g.k1 : g.k2) * 2;
+    return g;
+}
+
+// chunk jj of a tile: its layer, index within the layer, K width and byte offset in the packed weights
+__host__ __device__ inline void fused_chunk(const FusedGeom &g, int H, int jj, int &layer, int &c, int &kc,
+                                            size_t &off)
+{
+    const size_t b1 = (size_t)H * g.k1 * 2, b2 = (size_t)H * g.k2 * 2;
+    if (jj < g.nch1) { layer = 0; c = jj; kc = g.k1; off = c * b1; }
+    else if (jj < g.nch1 + g.nch2) { layer = 1; c = jj - g.nch1; kc = g.k2; off = g.nch1 * b1 + c * b2; }
+    else { layer = 2; c = jj - g.nch1 - g.nch2; kc = g.k2; off = g.nch1 * b1 + (g.nch2 + c) * b2; }
+}
 
 __device__ __forceinline__ void mbar_expect_tx_bytes(uint64_t *bar, uint32_t bytes)
 {
@@ -294,47 +330,78 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t *v)
     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
+// tcgen05.ld without the wait, and a pin that keeps the loaded registers from
+// being read before the wait (the empty asm "redefines" them after it)
+__device__ __forceinline__ void tmem_ld16_nowait(uint32_t taddr, uint32_t *v)
+{
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+        : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]), "=r"(v[8]),
+          "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
+        : "r"(taddr));
+}
+__device__ __forceinline__ void pin16(uint32_t *v)
+{
+    asm volatile("" : "+r"(v[0]), "+r"(v[1]), "+r"(v[2]), "+r"(v[3]), "+r"(v[4]), "+r"(v[5]), "+r"(v[6]), "+r"(v[7]),
+                 "+r"(v[8]), "+r"(v[9]), "+r"(v[10]), "+r"(v[11]), "+r"(v[12]), "+r"(v[13]), "+r"(v[14]), "+r"(v[15]));
+}
+// 16 * nb accumulator columns from c0 (nb <= 4) with a single wait
+__device__ __forceinline__ void tmem_ld_group(uint32_t taddr, int nb, uint32_t (*v)[16])
+{
+#pragma unroll
+    for (int b = 0; b < 4; ++b)
+        if (b < nb) tmem_ld16_nowait(taddr + 16u * b, v[b]);
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int b = 0; b < 4; ++b)
+        if (b < nb) pin16(v[b]);
+}
+
 // Pack W (layer l: [H x K_l] row-major BF16) into the chunked B-operand layout.
 // Chunk order: layer 1 chunks, layer 2 chunks, layer 3 chunks; K beyond K_l is zero.
 __global__ void fused_pack_kernel(const __nv_bfloat16 *__restrict__ w1, const __nv_bfloat16 *__restrict__ w2,
-                                  const __nv_bfloat16 *__restrict__ w3, int I, int H, int nch1, int nch2,
-                                  uint4 *__restrict__ out)
+                                  const __nv_bfloat16 *__restrict__ w3, int I, int H, uint4 *__restrict__ out)
 {
-    const int segs_per_chunk = H * (FKC / 8);
-    const int total = (nch1 + 2 * nch2) * segs_per_chunk;
-    for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < total; s += gridDim.x * blockDim.x) {
-        const int ch = s / segs_per_chunk, r = s % segs_per_chunk;
-        const int kb = r / H, n = r % H;   // 16-byte segment = row n of core matrix (n / 8, kb)
-        const __nv_bfloat16 *w;
-        int K, c;
-        if (ch < nch1) { w = w1; K = I; c = ch; }
-        else if (ch < nch1 + nch2) { w = w2; K = H; c = ch - nch1; }
-        else { w = w3; K = H; c = ch - nch1 - nch2; }
-        __nv_bfloat16 e[8];
+    const FusedGeom g = fused_geom(I, H);
+    for (int jj = blockIdx.y; jj < g.cpt; jj += gridDim.y) {
+        int layer, c, kc;
+        size_t off;
+        fused_chunk(g, H, jj, layer, c, kc, off);
+        const __nv_bfloat16 *w = layer == 0 ? w1 : (layer == 1 ? w2 : w3);
+        const int K = layer == 0 ? I : H;
+        const int segs = H * (kc / 8);
+        uint4 *dst = out + off / 16;
+        for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < segs; s += gridDim.x * blockDim.x) {
+            const int kb = s / H, n = s % H;   // 16-byte segment = row n of core matrix (n / 8, kb)
+            __nv_bfloat16 e[8];
 #pragma unroll
-        for (int q = 0; q < 8; ++q) {
-            const int k = c * FKC + kb * 8 + q;
-            e[q] = k < K ? w[(size_t)n * K + k] : __float2bfloat16(0.f);
+            for (int q = 0; q < 8; ++q) {
+                const int k = c * kc + kb * 8 + q;
+                e[q] = k < K ? w[(size_t)n * K + k] : __float2bfloat16(0.f);
+            }
+            // byte offset kb * H * 16 + (n / 8) * 128 + (n % 8) * 16 = (kb * H + n) * 16
+            dst[(size_t)kb * H + n] = *reinterpret_cast<const uint4 *>(e);
         }
-        // byte offset kb * H * 16 + (n / 8) * 128 + (n % 8) * 16 = (kb * H + n) * 16
-        out[(size_t)ch * segs_per_chunk + (size_t)kb * H + n] = *reinterpret_cast<const uint4 *>(e);
     }
 }
 
+// Two tiles (A and B) in flight: each has one activation buffer that holds its
+// input X for layer 1 and then the hidden activations, in the operand layout.
 struct FusedSmem {
-    int xs, hs, wb, par, nbuf, total;
+    int act0, act1, act_bytes, wb, par, nbuf, total;
 };
 
 __host__ __device__ inline FusedSmem fused_smem(int I, int H, int nbuf)
 {
     FusedSmem f;
-    const int nch1 = (I + FKC - 1) / FKC, nch2 = (H + FKC - 1) / FKC;
-    f.xs = 0;
-    f.hs = f.xs + nch1 * (FKC / 8) * 2048;
-    f.wb = f.hs + nch2 * (FKC / 8) * 2048;
-    f.par = f.wb + nbuf * H * FKC * 2;
+    const FusedGeom g = fused_geom(I, H);
+    f.act_bytes = (g.xkb > g.hkb ? g.xkb : g.hkb) * 2048;
+    f.act0 = 0;
+    f.act1 = f.act_bytes;
+    f.wb = 2 * f.act_bytes;
+    f.par = f.wb + nbuf * g.max_chunk_bytes;
     f.nbuf = nbuf;
-    f.total = f.par + (4 * H + 2 * 128 + 4) * 4;
+    f.total = f.par + (4 * H + 4) * 4;
     return f;
 }
 
@@ -371,23 +438,25 @@ fused_mlp_forward_kernel(const __nv_bfloat16 *__restrict__ X, int M, int I, int 
     __shared__ uint32_t tmem_base_sh;
     __shared__ int fail_sh;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int nch1 = (I + FKC - 1) / FKC, nch2 = (H + FKC - 1) / FKC, cpt = nch1 + 2 * nch2;
+    const FusedGeom G = fused_geom(I, H);
+    const int nch1 = G.nch1, nch2 = G.nch2, cpt = G.cpt;
     const FusedSmem L = fused_smem(I, H, nbuf);
-    unsigned char *xs = smem + L.xs, *hs = smem + L.hs, *wb = smem + L.wb;
-    float *par = reinterpret_cast<float *>(smem + L.par);   // b1 | b2 | b3 | w4 | red[2][128] | b4
-    float *red = par + 4 * H;
-    const uint32_t chunk_bytes = (uint32_t)H * FKC * 2;
+    unsigned char *act[2] = {smem + L.act0, smem + L.act1};
+    unsigned char *wb = smem + L.wb;
+    float *par = reinterpret_cast<float *>(smem + L.par);   // b1 | b2 | b3 | w4 | b4
+    const uint32_t buf_bytes = (uint32_t)G.max_chunk_bytes;   // ring buffer stride
     const int ntiles = (M + 127) / 128;
-    const int my_tiles = blockIdx.x < ntiles ? (ntiles - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
-    const long long total = (long long)my_tiles * cpt;   // weight chunks this CTA consumes
+    const int npairs = (ntiles + 1) / 2;
+    const int my_pairs = blockIdx.x < npairs ? (npairs - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
+    const long long total = (long long)my_pairs * cpt;   // weight chunks this CTA consumes
 
     for (int i = tid; i < H; i += FTHREADS) {
         par[i] = b1[i]; par[H + i] = b2[i]; par[2 * H + i] = b3[i]; par[3 * H + i] = w4[i];
     }
-    if (tid == 0) red[256] = b4[0];
+    if (tid == 0) par[4 * H] = b4[0];
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base_sh)),
-                     "r"(TMEM_COLS)
+                     "r"(2 * TMEM_COLS)
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
@@ -404,7 +473,7 @@ fused_mlp_forward_kernel(const __nv_bfloat16 *__restrict__ X, int M, int I, int 
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    const uint32_t tmem = tmem_base_sh;
+    const uint32_t tmem = tmem_base_sh;   // tile A's accumulator at column 0, tile B's at column 256
     const uint32_t idesc = instr_desc(128, H);
 
     // producer state (thread 0): chunks are loaded nbuf ahead; each barrier's
@@ -414,30 +483,34 @@ fused_mlp_forward_kernel(const __nv_bfloat16 *__restrict__ X, int M, int I, int 
     uint32_t tma_ph = 0, mma_ph = 0;   // bit b: parity of the next wait on buffer b
     auto load_chunk = [&](long long j) {
         const int b = (int)(j % nbuf);
-        mbar_expect_tx_bytes(&tma_bar[b], chunk_bytes);
-        bulk_g2s(wb + (size_t)b * chunk_bytes, wpack + (size_t)(j % cpt) * (chunk_bytes / 16), chunk_bytes,
-                 &tma_bar[b]);
+        int layer, c, kc;
+        size_t off;
+        fused_chunk(G, H, (int)(j % cpt), layer, c, kc, off);
+        const uint32_t bytes = (uint32_t)H * kc * 2;
+        mbar_expect_tx_bytes(&tma_bar[b], bytes);
+        bulk_g2s(wb + (size_t)b * buf_bytes, wpack + off / 16, bytes, &tma_bar[b]);
     };
-    // issue the MMAs of the next chunk; returns false if a bounded wait gave up
+    // issue the MMAs of the next chunk for both tiles; false if a bounded wait gave up
     auto consume_chunk = [&]() -> bool {
         const long long j = consumed;
         const int b = (int)(j % nbuf);
         if (!mbar_wait(&tma_bar[b], (tma_ph >> b) & 1u)) return false;
         tma_ph ^= 1u << b;
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        const int jj = (int)(j % cpt);
-        const int layer = jj < nch1 ? 0 : (jj < nch1 + nch2 ? 1 : 2);
-        const int c = layer == 0 ? jj : (layer == 1 ? jj - nch1 : jj - nch1 - nch2);
+        int layer, c, kc;
+        size_t off;
+        fused_chunk(G, H, (int)(j % cpt), layer, c, kc, off);
         const int K = layer == 0 ? I : H;
-        const unsigned char *A = layer == 0 ? xs : hs;
-        const unsigned char *B = wb + (size_t)b * chunk_bytes;
-#pragma unroll
-        for (int s = 0; s < FKC / 16; ++s) {
-            const int k = c * FKC + s * 16;
+        const unsigned char *B = wb + (size_t)b * buf_bytes;
+        for (int s = 0; s < kc / 16; ++s) {
+            const int k = c * kc + s * 16;
             if (k >= K) break;
-            const uint64_t ad = smem_desc(A + (size_t)(k / 8) * 2048, 2048, 128);
             const uint64_t bd = smem_desc(B + (size_t)(2 * s) * H * 16, (uint32_t)H * 16, 128);
-            tc_mma(tmem, ad, bd, idesc, (c > 0 || s > 0) ? 1u : 0u);
+            const uint32_t acc = (c > 0 || s > 0) ? 1u : 0u;
+#pragma unroll
+            for (int t = 0; t < 2; ++t)
+                tc_mma(tmem + (uint32_t)(t * TMEM_COLS), smem_desc(act[t] + (size_t)(k / 8) * 2048, 2048, 128), bd,
+                       idesc, acc);
         }
         tc_commit(&mma_bar[b]);
         consumed = j + 1;
@@ -453,18 +526,19 @@ fused_mlp_forward_kernel(const __nv_bfloat16 *__restrict__ X, int M, int I, int 
 
     if (tid == 0)
         while (loaded < total && loaded < nbuf) load_chunk(loaded++);
-    const int q = warp & 3, half = warp >> 2;
+    // epilogue roles: warp w reads TMEM lanes 32 (w % 4) .. +31 of tile w / 4
+    const int q = warp & 3, t_ep = warp >> 2;
     const int row_in_tile = 32 * q + lane;
-    const int hcols = H / 2;
     uint32_t layer_ph = 0;
     bool ok = true;
-    if (my_tiles > 0) fused_stage_x(xs, X, M, I, nch1 * (FKC / 8), (int)blockIdx.x * 128, tid, FTHREADS);
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    __syncthreads();
-
-    for (int t = 0; t < my_tiles && ok; ++t) {
-        const int tile = (int)blockIdx.x + t * (int)gridDim.x;
-        const int next = tile + (int)gridDim.x;
+    for (int p = 0; p < my_pairs && ok; ++p) {
+        const int pair = (int)blockIdx.x + p * (int)gridDim.x;
+        // both tiles' inputs into their activation buffers (the last layer's MMAs of the
+        // previous pair, the readers of these buffers, completed before its epilogue)
+        fused_stage_x(act[0], X, M, I, G.xkb, (2 * pair) * 128, tid, FTHREADS);
+        fused_stage_x(act[1], X, M, I, G.xkb, (2 * pair + 1) * 128, tid, FTHREADS);
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        __syncthreads();
         for (int layer = 0; layer < 3 && ok; ++layer) {
             const int nchunks = layer == 0 ? nch1 : nch2;
             if (tid == 0) {
@@ -473,10 +547,6 @@ fused_mlp_forward_kernel(const __nv_bfloat16 *__restrict__ X, int M, int I, int 
                 for (int c = 0; c < nchunks && good; ++c) good = consume_chunk();
                 if (good) tc_commit(&layer_bar);
                 else fail_sh = 1;
-            } else if (layer == 1 && next < ntiles && tid >= 32) {
-                // layer 1's MMAs are done (its epilogue waited for them): X of the next tile can go in
-                fused_stage_x(xs, X, M, I, nch1 * (FKC / 8), next * 128, tid - 32, FTHREADS - 32);
-                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
             }
             __syncwarp();
             const bool got = (volatile int &)fail_sh == 0 && mbar_wait(&layer_bar, layer_ph);
@@ -484,41 +554,58 @@ fused_mlp_forward_kernel(const __nv_bfloat16 *__restrict__ X, int M, int I, int 
             ok = __syncthreads_and(got ? 1 : 0) != 0;
             if (!ok) break;
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            const uint32_t taddr = tmem + ((uint32_t)(32 * q) << 16);
+            const uint32_t taddr = tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(t_ep * TMEM_COLS);
             const float *bias = par + layer * H;
             if (layer < 2) {
-                for (int c0 = half * hcols; c0 < (half + 1) * hcols; c0 += 16) {
-                    uint32_t v[16];
-                    tmem_ld16(taddr + (uint32_t)c0, v);
-                    float x[16];
+                unsigned char *dst0 = act[t_ep] + (row_in_tile >> 3) * 128 + (row_in_tile & 7) * 16;
+                for (int c0 = 0; c0 < H; c0 += 64) {
+                    const int nb = min(4, (H - c0) / 16);
+                    uint32_t v[4][16];
+                    tmem_ld_group(taddr + (uint32_t)c0, nb, v);
 #pragma unroll
-                    for (int e = 0; e < 16; ++e) x[e] = fmaxf(__uint_as_float(v[e]) + bias[c0 + e], 0.f);
-                    const int r = row_in_tile;
-                    unsigned char *dst = hs + (size_t)(c0 / 8) * 2048 + (r >> 3) * 128 + (r & 7) * 16;
-                    *reinterpret_cast<uint4 *>(dst) = pack8_bf16(x);
-                    *reinterpret_cast<uint4 *>(dst + 2048) = pack8_bf16(x + 8);
+                    for (int b = 0; b < 4; ++b) {
+                        if (b >= nb) break;
+                        const int cb = c0 + 16 * b;
+                        const float4 *b4v = reinterpret_cast<const float4 *>(bias + cb);
+                        float x[16];
+#pragma unroll
+                        for (int qq = 0; qq < 4; ++qq) {
+                            const float4 bb = b4v[qq];
+                            x[4 * qq] = fmaxf(__uint_as_float(v[b][4 * qq]) + bb.x, 0.f);
+                            x[4 * qq + 1] = fmaxf(__uint_as_float(v[b][4 * qq + 1]) + bb.y, 0.f);
+                            x[4 * qq + 2] = fmaxf(__uint_as_float(v[b][4 * qq + 2]) + bb.z, 0.f);
+                            x[4 * qq + 3] = fmaxf(__uint_as_float(v[b][4 * qq + 3]) + bb.w, 0.f);
+                        }
+                        unsigned char *dst = dst0 + (size_t)(cb / 8) * 2048;
+                        *reinterpret_cast<uint4 *>(dst) = pack8_bf16(x);
+                        *reinterpret_cast<uint4 *>(dst + 2048) = pack8_bf16(x + 8);
+                    }
                 }
                 asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
             } else {
                 float acc = 0.f;
                 const float *wv = par + 3 * H;
-                for (int c0 = half * hcols; c0 < (half + 1) * hcols; c0 += 16) {
-                    uint32_t v[16];
-                    tmem_ld16(taddr + (uint32_t)c0, v);
+                for (int c0 = 0; c0 < H; c0 += 64) {
+                    const int nb = min(4, (H - c0) / 16);
+                    uint32_t v[4][16];
+                    tmem_ld_group(taddr + (uint32_t)c0, nb, v);
 #pragma unroll
-                    for (int e = 0; e < 16; ++e) {
-                        const float h = __bfloat162float(__float2bfloat16(fmaxf(__uint_as_float(v[e]) + bias[c0 + e], 0.f)));
-                        acc = fmaf(h, wv[c0 + e], acc);
+                    for (int b = 0; b < 4; ++b) {
+                        if (b >= nb) break;
+                        const int cb = c0 + 16 * b;
+#pragma unroll
+                        for (int e = 0; e < 16; ++e) {
+                            const float h =
+                                __bfloat162float(__float2bfloat16(fmaxf(__uint_as_float(v[b][e]) + bias[cb + e], 0.f)));
+                            acc = fmaf(h, wv[cb + e], acc);
+                        }
                     }
                 }
-                red[half * 128 + row_in_tile] = acc;
+                const int row = (2 * pair + t_ep) * 128 + row_in_tile;
+                if (row < M) y[row] = acc + par[4 * H];
             }
             asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
             __syncthreads();
-            if (layer == 2 && half == 0) {
-                const int row = tile * 128 + row_in_tile;
-                if (row < M) y[row] = red[row_in_tile] + red[128 + row_in_tile] + red[256];
-            }
         }
     }
     if (!ok) {
@@ -536,7 +623,7 @@ fused_mlp_forward_kernel(const __nv_bfloat16 *__restrict__ X, int M, int I, int 
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     if (warp == 0)
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS) : "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(2 * TMEM_COLS) : "memory");
 }
 
 // ---- elementwise kernels of the MLP ---------------------------------------
@@ -674,17 +761,17 @@ int fused_mlp_nbuf(int I, int H)
 
 size_t fused_mlp_pack_bytes(int I, int H)
 {
-    const int nch1 = (I + mlp::FKC - 1) / mlp::FKC, nch2 = (H + mlp::FKC - 1) / mlp::FKC;
-    return (size_t)(nch1 + 2 * nch2) * H * mlp::FKC * 2;
+    const mlp::FusedGeom g = mlp::fused_geom(I, H);
+    return (size_t)H * 2 * ((size_t)g.nch1 * g.k1 + 2 * (size_t)g.nch2 * g.k2);
 }
 
 cudaError_t launch_fused_pack(const void *w1, const void *w2, const void *w3, int I, int H, void *out, cudaStream_t s)
 {
-    const int nch1 = (I + mlp::FKC - 1) / mlp::FKC, nch2 = (H + mlp::FKC - 1) / mlp::FKC;
-    mlp::fused_pack_kernel<<<128, 256, 0, s>>>(reinterpret_cast<const __nv_bfloat16 *>(w1),
-                                               reinterpret_cast<const __nv_bfloat16 *>(w2),
-                                               reinterpret_cast<const __nv_bfloat16 *>(w3), I, H, nch1, nch2,
-                                               reinterpret_cast<uint4 *>(out));
+    const int cpt = mlp::fused_geom(I, H).cpt;
+    mlp::fused_pack_kernel<<<dim3(32, cpt), 256, 0, s>>>(reinterpret_cast<const __nv_bfloat16 *>(w1),
+                                                         reinterpret_cast<const __nv_bfloat16 *>(w2),
+                                                         reinterpret_cast<const __nv_bfloat16 *>(w3), I, H,
+                                                         reinterpret_cast<uint4 *>(out));
     return cudaGetLastError();
 }
 
@@ -701,8 +788,8 @@ cudaError_t launch_fused_mlp_forward(const void *x, int M, int I, int H, const v
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    const int ntiles = (M + 127) / 128;
-    const int grid = std::max(1, std::min(ntiles, sms));
+    const int npairs = ((M + 127) / 128 + 1) / 2;
+    const int grid = std::max(1, std::min(npairs, sms));
     mlp::fused_mlp_forward_kernel<<<grid, mlp::FTHREADS, smem, s>>>(
         reinterpret_cast<const __nv_bfloat16 *>(x), M, I, H, reinterpret_cast<const uint4 *>(wpack), b1, b2, b3, w4,
         b4, y, nbuf, err);
