@@ -252,6 +252,15 @@ def run_learned(args, ws, rank, local):
     S.close()
 
 
+def rank_instances(workload: str, seed: int, rank: int, n_inst: int):
+    """The instances one rank searches: replicas, each rank its own (no data exchange)."""
+    from paper_1909_10286_gb300 import instances as I
+
+    if workload == "batched":
+        return I.make_batch("batched", range(seed * 1000 + rank * n_inst, seed * 1000 + (rank + 1) * n_inst))
+    return [I.make_instance(workload, seed + rank)]
+
+
 def run_reference(args, ws, rank):
     if rank != 0:
         return
@@ -265,12 +274,12 @@ def run_reference(args, ws, rank):
     o = O.Oracle(inst)
     op = O.make_params(**kw)
     st = o.start(op)
-    # sample size: the whole run (warm-up + steps) within about two minutes
+    # sample size: the whole run (warm-up + steps) within about --ref-budget seconds
     probe = min(n, 8192)
     t0 = time.perf_counter()
     o.search(op, st.copy(), 1, probe, threads=threads)
     rate = probe / max(time.perf_counter() - t0, 1e-6)
-    m = int(min(n, max(1024, rate * 120.0 / max(1, args.steps + args.warmup))))
+    m = int(min(n, max(1024, rate * args.ref_budget / max(1, args.steps + args.warmup))))
     o.search(op, st, args.warmup, m, threads=threads)
     t0 = time.perf_counter()
     o.search(op, st, args.steps, m, threads=threads)
@@ -303,6 +312,7 @@ def main():
     ap.add_argument("--no-time-to-target", action="store_true",
                     help="skip the time-to-1%% study (paper workload, rank 0, one GPU)")
     ap.add_argument("--study", action="store_true", help="print only the time-to-1%% study for --workload")
+    ap.add_argument("--ref-budget", type=float, default=120.0, help="seconds of oracle work in --impl reference")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     ws, rank, local = _dist()
@@ -333,9 +343,8 @@ def main():
     kw = dict(eps=0.5, seed=1000 + args.seed + rank, gate=1)
     stream = torch.cuda.Stream()
     tuned = None
+    insts = rank_instances(args.workload, args.seed, rank, args.n_inst)
     if args.workload == "batched":
-        insts = I.make_batch("batched", range(args.seed * 1000 + rank * args.n_inst,
-                                             args.seed * 1000 + (rank + 1) * args.n_inst))
         if args.no_autotune:
             params = biolog.make_params(n_cand=n, **kw)
         else:
@@ -344,7 +353,6 @@ def main():
             params = biolog.make_params(n_cand=n, blocks_per_sm=tuned["blocks_per_sm"], tile=tuned["tile"],
                                         lanes_per_cand=tuned.get("lanes_per_cand", 1), **kw)
     else:
-        insts = [I.make_instance(args.workload, args.seed + rank)]
         params = biolog.make_params(n_cand=n, **kw)
     inst = insts[0]
     n_total = n * len(insts)
