@@ -785,6 +785,10 @@ static void score_plan(const or_ctx *c, const or_params *prm, const oplan *p, do
     hu_assign(c, prm, &ra, act, na, hu_tour, R, Tc, &margin, &ops);
     double tmax = -INFINITY;
     for (int j = 0; j < na; ++j) { if (Tc[act[j]] > tmax) tmax = Tc[act[j]]; ops += 1; }
+    /* Model operations a result needs: Tmax depends on the HU assignment alone, so a
+       candidate the gate discards is decided here (its C is +inf whatever follows); the
+       rest is computed for every candidate all the same, only not counted for those. */
+    const double ops_at_gate = ops;
     su_assign(c, prm, &ra, act, na, R, su_tour, Tw, &margin, &ops);
 
     /* Third step: the path-length cost (Sec. 2.2). N_HU(g) multiplies the HU
@@ -834,7 +838,10 @@ static void score_plan(const or_ctx *c, const or_params *prm, const oplan *p, do
     if (gate) {
         note_gap(&margin, tmax, tmax_star, fmax(tmax, tmax_star));
         ops += 1;
-        if ((gate == 1 && tmax > tmax_star) || (gate == 2 && tmax >= tmax_star)) cost = INFINITY;
+        if ((gate == 1 && tmax > tmax_star) || (gate == 2 && tmax >= tmax_star)) {
+            cost = INFINITY;
+            ops = ops_at_gate + 1;
+        }
     }
     res->cost = cost;
     res->margin = margin;

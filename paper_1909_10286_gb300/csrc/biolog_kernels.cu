@@ -131,7 +131,7 @@ struct Shape {
 };
 
 #ifndef BIOLOG_SHAPEA_MINB
-#define BIOLOG_SHAPEA_MINB 3
+#define BIOLOG_SHAPEA_MINB 2
 #endif
 using ShapeA = Shape<4, 0, true, 256, BIOLOG_SHAPEA_MINB>;   // <= 4 tours, <= 32 HUs/SUs, 32-bit sums
 using ShapeB = Shape<8, 1, true, 128, 4>;                     // <= 8 tours, <= 64 HUs/SUs
@@ -534,8 +534,11 @@ struct TourState {
 
 // Per-candidate scoring. DUMP: the inspection kernel's full per-tour report;
 // IDENT: the base plan's own T_compl, shuttle ratio and shuttle sum per active
-// tour (o_tc, o_kf, o_sh), written without local arrays.
-template <class SH, bool DUMP, bool IDENT = false>
+// tour (o_tc, o_kf, o_sh), written without local arrays. STAGE 1: only as far
+// as the completion-time gate (route aggregates, HU assignment, Tmax): the cost
+// is +inf if the gate discards the candidate, else 0 (not a cost); Tmax depends
+// on the HU assignment alone, so the gate decision is final at that point.
+template <class SH, bool DUMP, bool IDENT = false, int STAGE = 0>
 __device__ ScoreOut score_candidate(const Ctx &c, const SearchParams &p, const MoveRec &m, float tmax_star,
                                     unsigned char *tstate, int tid, int16_t *o_nhu, int16_t *o_nsu, float *o_tc,
                                     float *o_tw, float *o_tcost, int16_t *o_hu, int16_t *o_su, float *o_kf = nullptr,
@@ -645,6 +648,12 @@ __device__ ScoreOut score_candidate(const Ctx &c, const SearchParams &p, const M
     }
     if constexpr (IDENT) {
         FOR_ACTIVE(g) o_tc[g] = tv[g];
+    }
+    if constexpr (STAGE == 1) {
+        out.cost = ((p.gate == 1 && tmax > tmax_star) || (p.gate == 2 && tmax >= tmax_star)) ? __int_as_float(0x7f800000)
+                                                                                              : 0.f;
+        out.tmax = tmax;
+        return out;
     }
 
     // --- SU assignment (Algorithm 2, Eq. 6). R(g) is fixed now: one reciprocal per tour.
@@ -881,7 +890,8 @@ __device__ ScoreOut score_candidate(const Ctx &c, const SearchParams &p, const M
 __host__ __device__ inline size_t align16(size_t x) { return (x + 15) & ~size_t(15); }
 
 struct SmemPlan {
-    size_t off_blob, off_plan, off_derived, off_supq, off_bad, off_base_agg, off_tour, off_qidx, off_qmv, total;
+    size_t off_blob, off_plan, off_derived, off_supq, off_bad, off_base_agg, off_tour, off_qidx, off_qmv, off_qidx2,
+        off_qmv2, total;
 };
 
 __host__ __device__ inline SmemPlan carve(size_t tour_bytes, int threads, int max_prefix, int max_plan_len, int max_F,
@@ -899,6 +909,8 @@ __host__ __device__ inline SmemPlan carve(size_t tour_bytes, int threads, int ma
     s.off_tour = o; o += align16(tour_bytes);
     s.off_qidx = o; o += align16((size_t)(threads / 32) * WQ * 4);
     s.off_qmv = o; o += align16((size_t)(threads / 32) * WQ * 8);
+    s.off_qidx2 = o; o += align16((size_t)(threads / 32) * WQ * 4);   // candidates that passed the gate
+    s.off_qmv2 = o; o += align16((size_t)(threads / 32) * WQ * 8);
     s.total = o;
     return s;
 }
@@ -1231,6 +1243,8 @@ __global__ void __launch_bounds__(SH::NT, SH::MINB) search_iteration_kernel(cons
     unsigned char *tstate = smem + sp.off_tour;
     int32_t *qidx = (int32_t *)(smem + sp.off_qidx) + warp * WQ;
     int2 *qmv = (int2 *)(smem + sp.off_qmv) + warp * WQ;
+    int32_t *qidx2 = (int32_t *)(smem + sp.off_qidx2) + warp * WQ;
+    int2 *qmv2 = (int2 *)(smem + sp.off_qmv2) + warp * WQ;
     Ctx c;
     for (int w = blockIdx.x; w < n_work; w += gridDim.x) {
         const WorkItem wi = work[w];
@@ -1252,9 +1266,14 @@ __global__ void __launch_bounds__(SH::NT, SH::MINB) search_iteration_kernel(cons
         const int c1 = min(c0 + tl, cand_list ? min(M.n_cand, list_n) : M.n_cand);
         unsigned long long best = ~0ull;
         float best_t = 0.f;
-        // each warp: draw 32 moves at a time, queue the feasible ones, score 32 queued at a time
-        int qhead = 0, qcount = 0;   // warp-uniform ring-buffer state
-        for (int base = c0 + warp * 32; base < c1 || qcount > 0; base += NT) {
+        // each warp: draw 32 moves at a time and queue the feasible ones (Eq. 2); take 32 queued
+        // at a time as far as the completion-time gate and queue those it keeps; score 32 of
+        // those at a time in full. The gate discards most feasible candidates: their cost is
+        // +inf once Tmax is known, and the SU assignment and shuttle pass run in full warps
+        // of the others only.
+        int qhead = 0, qcount = 0;     // warp-uniform ring-buffer state, feasible candidates
+        int q2head = 0, q2count = 0;   // candidates the gate kept
+        for (int base = c0 + warp * 32; base < c1 || qcount > 0 || q2count > 0; base += NT) {
             // (c1 may be below c0 in list mode: then the work item only reports an empty slot)
             if (base < c1) {
                 const int pos = base + lane;
@@ -1278,13 +1297,46 @@ __global__ void __launch_bounds__(SH::NT, SH::MINB) search_iteration_kernel(cons
                 qcount += __popc(ball);
                 __syncwarp();
             }
-            // score a full warp of queued candidates, or the remainder once the draws are done
-            const int take = (qcount >= 32) ? 32 : ((base + NT >= c1) ? qcount : 0);
+            const bool drained = base + NT >= c1;   // no more draws
+            // up to the gate for a full warp of feasible candidates, or the remainder once drained
+            const int take = (qcount >= 32) ? 32 : (drained ? qcount : 0);
             if (take > 0) {
+                bool kept = false;
+                int i = 0;
+                int2 pm = make_int2(0, 0);
                 if (lane < take) {
                     const int slot = (qhead + lane) & (WQ - 1);
-                    const int i = qidx[slot];
-                    const int2 pm = qmv[slot];
+                    i = qidx[slot];
+                    pm = qmv[slot];
+                    const MoveRec m = {pm.x & 0xffff, pm.x >> 16, pm.y & 0xffff, pm.y >> 16};
+                    const ScoreOut r = score_candidate<SH, false, false, 1>(c, prm, m, tmax_star, tstate, tid, nullptr,
+                                                                           nullptr, nullptr, nullptr, nullptr, nullptr,
+                                                                           nullptr);
+                    if (isinf(r.cost)) {   // discarded by the gate: C = +inf (Sec. 2.5)
+                        const unsigned long long k = make_key(r.cost, (uint32_t)i);
+                        if (k < best) { best = k; best_t = r.tmax; }
+                    } else {
+                        kept = true;
+                    }
+                }
+                const unsigned ball = __ballot_sync(0xffffffffu, kept);
+                if (kept) {
+                    const int slot = (q2head + q2count + __popc(ball & ((1u << lane) - 1u))) & (WQ - 1);
+                    qidx2[slot] = i;
+                    qmv2[slot] = pm;
+                }
+                q2count += __popc(ball);
+                __syncwarp();
+                qhead = (qhead + take) & (WQ - 1);
+                qcount -= take;
+            }
+            // the full score of a warp of candidates the gate kept, or the remainder at the end
+            const int take2 = (q2count >= 32) ? 32 : ((drained && qcount == 0) ? q2count : 0);
+            if (take2 > 0) {
+                if (lane < take2) {
+                    const int slot = (q2head + lane) & (WQ - 1);
+                    const int i = qidx2[slot];
+                    const int2 pm = qmv2[slot];
                     const MoveRec m = {pm.x & 0xffff, pm.x >> 16, pm.y & 0xffff, pm.y >> 16};
                     const ScoreOut r = score_candidate<SH, false>(c, prm, m, tmax_star, tstate, tid, nullptr, nullptr,
                                                                   nullptr, nullptr, nullptr, nullptr, nullptr);
@@ -1292,8 +1344,8 @@ __global__ void __launch_bounds__(SH::NT, SH::MINB) search_iteration_kernel(cons
                     if (k < best) { best = k; best_t = r.tmax; }
                 }
                 __syncwarp();
-                qhead = (qhead + take) & (WQ - 1);
-                qcount -= take;
+                q2head = (q2head + take2) & (WQ - 1);
+                q2count -= take2;
             }
         }
         block_argmin_finalize<NT>(best, best_t, bs, M, wi, slot_key, slot_tmax, slot_base, c, prm, iter);
@@ -1523,6 +1575,12 @@ __device__ ScoreOut score_coop(const Ctx &c, const SearchParams &p, const MoveRe
     }
     const float tmax = grp_max<L>(act ? tv : -INFINITY, gm);
     if (IDENT && act) o_tc[g] = tv;
+    // the gate depends on Tmax alone: a discarded candidate's cost is +inf (Sec. 2.5)
+    if (!IDENT && ((p.gate == 1 && tmax > tmax_star) || (p.gate == 2 && tmax >= tmax_star))) {
+        out.cost = __int_as_float(0x7f800000);
+        out.tmax = tmax;
+        return out;
+    }
 
     // --- SU assignment (Algorithm 2, Eq. 6); R(g) is fixed now
     M S0 = 0;
