@@ -79,6 +79,83 @@ def _max_over_ranks(x: float, ws: int) -> float:
     return float(t.item())
 
 
+class NvmlSampler:
+    """SM clock, power and clock-event reasons read through NVML (libnvidia-ml)
+    every ~2 ms in a thread, so that a timed region of a few milliseconds gets
+    samples inside it. Read-only: nothing on the GPU is changed."""
+
+    BITS = {"sw_power_cap": 0x4, "hw_slowdown": 0x8, "sw_thermal_slowdown": 0x20, "hw_thermal_slowdown": 0x40}
+
+    def __init__(self, device_index: int):
+        import ctypes as C
+        import threading
+
+        self.C, self.lib, self.h = C, None, None
+        self.samples = []
+        self.stop_evt = threading.Event()
+        self.thread = None
+        for name in ("libnvidia-ml.so.1", "libnvidia-ml.so"):
+            try:
+                self.lib = C.CDLL(name)
+                break
+            except OSError:
+                continue
+        if self.lib is None or self.lib.nvmlInit_v2() != 0:
+            self.lib = None
+            return
+        h = C.c_void_p()
+        try:
+            import torch
+            p = torch.cuda.get_device_properties(device_index)
+            bus = f"{p.pci_domain_id:08x}:{p.pci_bus_id:02x}:{p.pci_device_id:02x}.0".encode()
+            ok = self.lib.nvmlDeviceGetHandleByPciBusId_v2(C.c_char_p(bus), C.byref(h)) == 0
+        except Exception:
+            ok = False
+        if not ok and self.lib.nvmlDeviceGetHandleByIndex_v2(C.c_uint(device_index), C.byref(h)) != 0:
+            self.lib = None
+            return
+        self.h = h
+        self.reasons_fn = getattr(self.lib, "nvmlDeviceGetCurrentClocksEventReasons", None) or \
+            self.lib.nvmlDeviceGetCurrentClocksThrottleReasons
+
+    def ok(self) -> bool:
+        return self.lib is not None
+
+    def _run(self):
+        C = self.C
+        mhz, mw, rs = C.c_uint(), C.c_uint(), C.c_ulonglong()
+        while not self.stop_evt.is_set():
+            if (self.lib.nvmlDeviceGetClockInfo(self.h, 1, C.byref(mhz)) == 0 and
+                    self.reasons_fn(self.h, C.byref(rs)) == 0):
+                self.lib.nvmlDeviceGetPowerUsage(self.h, C.byref(mw))
+                self.samples.append((mhz.value, mw.value / 1000.0, rs.value))
+            self.stop_evt.wait(0.002)
+
+    def start(self):
+        import threading
+
+        self.thread = threading.Thread(target=self._run, daemon=True)
+        self.thread.start()
+
+    def stop(self) -> dict:
+        self.stop_evt.set()
+        self.thread.join(timeout=5)
+        mx = self.C.c_uint()
+        self.lib.nvmlDeviceGetMaxClockInfo(self.h, 1, self.C.byref(mx))
+        if not self.samples:
+            return {"sm_mhz": None, "sm_max_mhz": mx.value or None, "reasons": ["no samples"], "source": "nvml"}
+        reasons = sorted({n for _, _, r in self.samples for n, b in self.BITS.items() if r & b})
+        return {"sm_mhz": statistics.median(m for m, _, _ in self.samples), "sm_max_mhz": mx.value,
+                "reasons": reasons, "samples": len(self.samples),
+                "power_w_max": max(p for _, p, _ in self.samples), "source": "nvml, every ~2 ms"}
+
+
+def clock_sampler(device_index: int):
+    """NVML sampling where the library is present, else nvidia-smi."""
+    s = NvmlSampler(device_index)
+    return s if s.ok() else ClockSampler(device_index)
+
+
 class ClockSampler:
     """nvidia-smi clock samples during the timed region."""
 
@@ -189,7 +266,7 @@ def run_learned(args, ws, rank, local):
     torch.cuda.synchronize()
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
     evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-    clocks = ClockSampler(local)
+    clocks = clock_sampler(local)
     clocks.start()
     _barrier(ws)
     torch.cuda.synchronize()
@@ -363,7 +440,7 @@ def main():
     torch.cuda.synchronize()
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
     evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-    clocks = ClockSampler(local)
+    clocks = clock_sampler(local)
     clocks.start()
     _barrier(ws)
     torch.cuda.synchronize()
