@@ -297,6 +297,18 @@ int bl_features(bl_handle *h, int32_t inst, int32_t use_best, uint32_t iter, int
    pool buffers (pool x instances x 136 bytes). Asynchronous on the stream. */
 int bl_search_step_learned(bl_handle *h, bl_mlp *mlp, int32_t n_iters, int32_t pool, int32_t n_keep, float rand_frac);
 
+/* Self-test of the bounded device waits (plumbing; no counterpart in the
+   paper). Every wait of the library's kernels on a barrier or a bulk copy
+   gives up after a wall-clock limit, sets the handle's error flag and returns,
+   so that a lost completion turns into BL_ETIMEOUT on the host instead of a
+   hung GPU. This call runs one thread on `stream` that waits, with the limit
+   limit_ns (0 < limit_ns <= 10 s), on a barrier that nothing completes (no
+   copy or arrival is pending on it), and reports what happened: BL_ETIMEOUT
+   (expected: the wait gave up) with *elapsed_ns (may be NULL) the time it
+   waited, BL_OK if the wait unexpectedly completed, BL_EINVAL, BL_ECUDA.
+   Synchronises the stream; the context stays usable. */
+int bl_wait_selftest(void *stream, uint64_t limit_ns, uint64_t *elapsed_ns);
+
 /* Kernel configuration in use: threads per block, grid blocks, candidates
    per work item, the number of kernels one iteration launches, and the lanes
    that score one candidate (any pointer may be NULL). */

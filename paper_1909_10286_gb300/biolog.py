@@ -24,7 +24,7 @@ _lock = threading.Lock()
 BL_OK, BL_EINVAL, BL_EINFEASIBLE_INSTANCE, BL_ETOO_LARGE, BL_ECUDA, BL_ETIMEOUT, BL_ESTATE = 0, -1, -2, -3, -4, -5, -6
 EXPORTS = ("bl_workspace_bytes", "bl_plan_init", "bl_plan_init_batch", "bl_search_step", "bl_best_plan",
            "bl_get_state", "bl_set_state", "bl_get_log", "bl_score_candidates", "bl_decode_candidates",
-           "bl_get_config", "bl_plan_free", "bl_last_error", "bl_global_error", "bl_argmin_noalloc",
+           "bl_get_config", "bl_plan_free", "bl_last_error", "bl_global_error", "bl_argmin_noalloc", "bl_wait_selftest",
            "bl_mlp_create", "bl_mlp_forward", "bl_mlp_grads", "bl_mlp_train_step", "bl_mlp_get", "bl_mlp_set",
            "bl_mlp_free", "bl_mlp_last_error", "bl_gemm_bf16", "bl_features", "bl_search_step_learned")
 
@@ -89,6 +89,7 @@ def load(path: str | None = None):
                                               vp, vp, vp, vp, vp]
             L.bl_decode_candidates.argtypes = [vp, C.c_int32, C.c_int32, C.c_uint32, vp, C.c_int32, vp]
             L.bl_get_config.argtypes = [vp, vp, vp, vp, vp, vp]
+            L.bl_wait_selftest.argtypes = [vp, C.c_uint64, C.POINTER(C.c_uint64)]
             L.bl_argmin_noalloc.argtypes = [vp, C.c_int32, C.c_int32, C.c_uint32, C.c_float, C.c_int32, C.c_int32,
                                             vp, vp]
             L.bl_features.argtypes = [vp, C.c_int32, C.c_int32, C.c_uint32, C.c_int32, C.c_int32, vp, vp]
@@ -286,6 +287,16 @@ def plan_init_batch(instances, params: bl_params, stream=None) -> Search:
 
 def search_step(h: Search, n_iters: int):
     h.search_step(n_iters)
+
+
+def wait_selftest(limit_ns: int, stream=None) -> tuple[int, int]:
+    """bl_wait_selftest: (return code, nanoseconds waited); BL_ETIMEOUT is the expected code."""
+    import torch
+
+    s = stream if stream is not None else torch.cuda.current_stream()
+    el = C.c_uint64(0)
+    rc = load().bl_wait_selftest(C.c_void_p(s.cuda_stream), int(limit_ns), C.byref(el))
+    return int(rc), int(el.value)
 
 
 def best_plan(h: Search, inst: int = 0) -> dict:

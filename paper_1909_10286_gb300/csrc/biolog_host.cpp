@@ -734,6 +734,31 @@ const char *bl_global_error(void) { return g_error.c_str(); }
 
 const char *bl_last_error(const bl_handle *h) { return h ? h->err.c_str() : g_error.c_str(); }
 
+int bl_wait_selftest(void *stream, uint64_t limit_ns, uint64_t *elapsed_ns)
+{
+    if (limit_ns == 0 || limit_ns > 10000000000ull) {
+        g_error = "bl_wait_selftest: limit_ns in (0, 10 s]";
+        return BL_EINVAL;
+    }
+    unsigned long long *d = nullptr, hbuf[2] = {0ull, 0ull};
+    const cudaStream_t s = (cudaStream_t)stream;
+    cudaError_t e = cudaMalloc((void **)&d, sizeof(hbuf));
+    if (e == cudaSuccess) e = launch_wait_selftest(limit_ns, d, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(hbuf, d, sizeof(hbuf), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (d) cudaFree(d);
+    if (e != cudaSuccess) {
+        g_error = std::string("bl_wait_selftest: ") + cudaGetErrorString(e);
+        return BL_ECUDA;
+    }
+    if (elapsed_ns) *elapsed_ns = hbuf[1];
+    if (hbuf[0]) {
+        g_error = "bl_wait_selftest: the bounded wait gave up, as it should";
+        return BL_ETIMEOUT;
+    }
+    return BL_OK;
+}
+
 int bl_workspace_bytes(const bl_instance *insts, int32_t n_inst, const bl_params *params, size_t *bytes)
 {
     if (!bytes) { g_error = "null bytes"; return BL_EINVAL; }

@@ -141,6 +141,7 @@ size_t shared_bytes(int32_t shape, int32_t threads, int32_t max_prefix, int32_t 
                     int32_t max_B, int32_t max_T);
 cudaError_t configure_kernels(int32_t shape, size_t smem);
 int search_blocks_per_sm(int32_t shape, size_t smem);
+cudaError_t launch_wait_selftest(uint64_t limit_ns, unsigned long long *d_out, cudaStream_t s);
 // cooperative search kernel (lanes per candidate > 1)
 constexpr int kCoopThreads = 256;
 bool coop_supported(int32_t shape, int32_t lanes);

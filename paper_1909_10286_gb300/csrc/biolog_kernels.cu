@@ -100,15 +100,29 @@ __device__ __forceinline__ uint64_t global_ns()
     return t;
 }
 
-// bounded wait: gives up after ~1 s of wall time
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity)
+// bounded wait: gives up after limit_ns of wall time (1 s unless told otherwise)
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity, uint64_t limit_ns = 1000000000ull)
 {
     if (mbar_try_wait(bar, parity)) return true;
     const uint64_t t0 = global_ns();
     while (true) {
         if (mbar_try_wait(bar, parity)) return true;
-        if (global_ns() - t0 > 1000000000ull) return false;
+        if (global_ns() - t0 > limit_ns) return false;
     }
+}
+
+// Self-test of the bounded wait: one thread waits on a barrier that nothing
+// will ever complete (no copy, no arrival is pending on it), with a short
+// limit; out[0] = 1 if the wait gave up, out[1] = the nanoseconds it took.
+__global__ void wait_selftest_kernel(uint64_t limit_ns, unsigned long long *out)
+{
+    __shared__ uint64_t bar;
+    mbar_init(&bar, 1);
+    fence_mbar_init();
+    const uint64_t t0 = global_ns();
+    const bool done = mbar_wait_bounded(&bar, 0u, limit_ns);
+    out[0] = done ? 0ull : 1ull;
+    out[1] = global_ns() - t0;
 }
 
 // ---------------------------------------------------------------------------
@@ -2606,4 +2620,12 @@ cudaError_t launch_decode(const LaunchCfg &cfg, const InstMeta *d_meta, int32_t 
     return cudaGetLastError();
 }
 
+}  // namespace biolog
+
+namespace biolog {
+cudaError_t launch_wait_selftest(uint64_t limit_ns, unsigned long long *d_out, cudaStream_t s)
+{
+    wait_selftest_kernel<<<1, 1, 0, s>>>(limit_ns, d_out);
+    return cudaGetLastError();
+}
 }  // namespace biolog
