@@ -196,7 +196,7 @@ struct Ctx {
     // base plan, per tour: HU route, SU route, area (fixed point) and 2 x mean of per-BP means
     const long long *tLHU, *tLSU, *tA;
     const float *tDB2;
-    const int *dqown;                      // per base field position: distance to its own BP
+    const int2 *psd;                       // per base field position: {supply (float bits), distance to its BP}
     const float *kf_base;                  // base plan's shuttle ratio N_SU/sum cap per tour
     const long long *sh_base;              // base plan's shuttle sum per tour (fixed point)
     int memo;                              // 1 = reuse the base's shuttle sums where valid
@@ -816,6 +816,13 @@ __device__ ScoreOut score_candidate(const Ctx &c, const SearchParams &p, const M
         shq += v0;
     }
     if (fresh) {
+        // base positions of the fields that left their BP (added at their new BP below)
+        int skip0 = -1, skip1 = -1;
+        if (x.kind == 0 && x.sg != x.dg) skip0 = c.bp_start[x.sg] + c.field_pos[x.v];
+        if (x.kind == 2 && c.field_bp[x.v] != c.field_bp[x.w]) {
+            skip0 = c.bp_start[c.field_bp[x.v]] + c.field_pos[x.v];
+            skip1 = c.bp_start[c.field_bp[x.w]] + c.field_pos[x.w];
+        }
         for (int b = 0; b < c.B; ++b) {
             const int g = x.tour_of_bp(c, b);
             if (!((fresh >> g) & 1u)) continue;
@@ -826,10 +833,10 @@ __device__ ScoreOut score_candidate(const Ctx &c, const SearchParams &p, const M
             long long acc = 0;
             const int k0 = c.bp_start[b], k1 = k0 + c.bp_cnt[b];
             for (int kk = k0; kk < k1; ++kk) {
-                const int f = c.field_order[kk];
-                if (x.bp_of_field(c, f) != b) continue;   // moved to another BP: added below
-                const int n = ceil_n(g, c.supply[f], kf);
-                acc += (long long)n * (long long)c.dqown[kk];
+                if (kk == skip0 || kk == skip1) continue;
+                const int2 sd = c.psd[kk];
+                const int n = ceil_n(g, __int_as_float(sd.x), kf);
+                acc += (long long)n * (long long)sd.y;
             }
             shq += acc;
             if constexpr (DUMP) dSh[g] += acc;
@@ -919,7 +926,7 @@ __host__ __device__ inline SmemPlan carve(size_t tour_bytes, int threads, int ma
     s.off_supq = o; o += align16((size_t)max_B * 8);
     s.off_bad = o; o += align16((size_t)max_B);
     s.off_base_agg = o; o += align16((size_t)max_B * 3 * 8 + (size_t)max_T * (3 * 8 + 4 + 4) + (size_t)max_T * 8 +
-                                     (size_t)max_F * 4 + (size_t)max_B * 2 * 2);
+                                     (size_t)max_F * 8 + (size_t)max_B * 2 * 2);
     s.off_tour = o; o += align16(tour_bytes);
     s.off_qidx = o; o += align16((size_t)(threads / 32) * WQ * 4);
     s.off_qmv = o; o += align16((size_t)(threads / 32) * WQ * 8);
@@ -1030,12 +1037,12 @@ __device__ bool stage_base(const InstMeta &M, BlockShared &bs, unsigned char *sm
     float *tDB2 = (float *)(tA + T);
     float *kf_base = tDB2 + T;
     long long *sh_base = (long long *)(bt + (size_t)B * 3 * 8 + (size_t)T * (3 * 8 + 4 + 4));
-    int *dqown = (int *)(sh_base + T);
-    int16_t *bfirst = (int16_t *)(dqown + F), *blast = bfirst + B;
+    int2 *psd = (int2 *)(sh_base + T);
+    int16_t *bfirst = (int16_t *)(psd + F), *blast = bfirst + B;
     c.tour_start = tour_start; c.bp_start = bp_start; c.bp_tour = bp_tour; c.bp_pos = bp_pos;
     c.field_bp = field_bp; c.field_pos = field_pos; c.base_supq = base_supq; c.bad = bad;
     c.bint = bint; c.bsb = bsb; c.barea = barea; c.tLHU = tLHU; c.tLSU = tLSU; c.tA = tA; c.tDB2 = tDB2;
-    c.dqown = dqown; c.bfirst = bfirst; c.blast = blast; c.kf_base = kf_base; c.sh_base = sh_base; c.memo = 0;
+    c.psd = psd; c.bfirst = bfirst; c.blast = blast; c.kf_base = kf_base; c.sh_base = sh_base; c.memo = 0;
     if (tid == 0) {
         int s = 0;
         for (int g = 0; g < T; ++g) { tour_start[g] = (int16_t)s; s += c.tour_cnt[g]; }
@@ -1054,7 +1061,7 @@ __device__ bool stage_base(const InstMeta &M, BlockShared &bs, unsigned char *sm
             const int f = c.field_order[bp_start[b] + k];
             field_bp[f] = (int16_t)b; field_pos[f] = (int16_t)k;
             s += c.supq[f];
-            dqown[bp_start[b] + k] = c.Dq[(1 + B + f) * c.N + 1 + b];
+            psd[bp_start[b] + k] = make_int2(__float_as_int(c.supply[f]), c.Dq[(1 + B + f) * c.N + 1 + b]);
         }
         base_supq[b] = s;
         bad[b] = (int8_t)(s < c.demq[b] ? 1 : 0);
@@ -1731,7 +1738,7 @@ __device__ ScoreOut score_coop(const Ctx &c, const SearchParams &p, const MoveRe
                 const int b = c.field_bp[f];   // base BP of this position
                 if (x.bp_of_field(c, f) == b) {   // moved fields are added below
                     const int tb = x.tour_of_bp(c, b);
-                    if ((fresh >> tb) & 1u) { t = tb; sup = c.supply[f]; dq = c.dqown[kk]; }
+                    if ((fresh >> tb) & 1u) { const int2 sd = c.psd[kk]; t = tb; sup = __int_as_float(sd.x); dq = sd.y; }
                 }
             }
             const int src = t < 0 ? 0 : t;
