@@ -510,7 +510,24 @@ __device__ __forceinline__ long long cap_sum(const Ctx &c, typename SH::Mask s0,
 
 struct ScoreOut {
     float cost, tmax;
+    unsigned amask;   // active tours (STAGE 1)
 };
+
+// What the full score of a candidate that passed the gate needs from the first
+// stage (route aggregates and HU assignment), kept per queued candidate so the
+// full score does not repeat them: per tour the HU and SU route lengths, 2 x the
+// mean of per-BP means, the HU rate sum and the HU set; the active tours and Tmax.
+template <class SH>
+struct Survivor {
+    float lhu[SH::MAXT], lsu[SH::MAXT], db2[SH::MAXT];
+    typename SH::Sum rq[SH::MAXT];
+    typename SH::Mask hm[SH::MAXT];
+    unsigned amask;
+    float tmax;
+};
+// kept for shapes of at most 4 tours, where the records fit next to two blocks per SM
+template <class SH>
+constexpr bool kKeepSurvivors = SH::MAXT <= 4;
 
 // Per-thread per-tour state: one shared-memory column per value. (Completion
 // and waiting times live in registers during the local minimisations; the
@@ -552,17 +569,22 @@ struct TourState {
 // as the completion-time gate (route aggregates, HU assignment, Tmax): the cost
 // is +inf if the gate discards the candidate, else 0 (not a cost); Tmax depends
 // on the HU assignment alone, so the gate decision is final at that point.
+// STAGE 2: the rest of the score, resumed from a Survivor record of stage 1.
 template <class SH, bool DUMP, bool IDENT = false, int STAGE = 0>
 __device__ ScoreOut score_candidate(const Ctx &c, const SearchParams &p, const MoveRec &m, float tmax_star,
                                     unsigned char *tstate, int tid, int16_t *o_nhu, int16_t *o_nsu, float *o_tc,
                                     float *o_tw, float *o_tcost, int16_t *o_hu, int16_t *o_su, float *o_kf = nullptr,
-                                    long long *o_sh = nullptr)
+                                    long long *o_sh = nullptr, const Survivor<SH> *rec = nullptr)
 {
     constexpr int MAXT = SH::MAXT, SW = SH::SW;
     using M = typename SH::Mask;
     using S = typename SH::Sum;
     TourState<SH> ts;
     ts.bind(tstate, tid);
+    unsigned amask = 0;
+    int na = 0;
+    float tv[MAXT];   // the round's times, in registers for the picks
+    float tmax;
     // per-tour report (DUMP only): completion and waiting times, shuttle sums
     [[maybe_unused]] float dTc[MAXT], dTw[MAXT];
     [[maybe_unused]] long long dSh[MAXT];
@@ -571,10 +593,19 @@ __device__ ScoreOut score_candidate(const Ctx &c, const SearchParams &p, const M
     View x;
     x.set(c, m);
 
+    if constexpr (STAGE == 2) {
+        amask = rec->amask;
+        na = __popc(amask);
+        tmax = rec->tmax;
+#pragma unroll
+        for (int g = 0; g < MAXT; ++g)
+            if ((amask >> g) & 1u) {
+                ts.LHU.set(g, rec->lhu[g]); ts.LSU.set(g, rec->lsu[g]); ts.DB2.set(g, rec->db2[g]);
+                ts.Rq.set(g, rec->rq[g]); ts.Hm.set(g, rec->hm[g]);
+            }
+    } else {
     // --- route aggregates (Fig. 1, Sec. 2.2): rebuild the touched tours, reuse the base's
     const unsigned touched = x.touched(c);
-    unsigned amask = 0;
-    int na = 0;
     for (int g = 0; g < c.T; ++g) {
         const int nb = x.tour_len(c, g);
         if (nb == 0) continue;
@@ -597,7 +628,6 @@ __device__ ScoreOut score_candidate(const Ctx &c, const SearchParams &p, const M
     const int g_first = __ffs(amask) - 1;
 
     // --- HU assignment (Sec. 2.5): round-robin dealing, then Algorithm 2 on T_compl
-    float tv[MAXT];   // the round's times, in registers for the picks
     {
         int j = 0;
         FOR_ACTIVE(g) {
@@ -651,7 +681,7 @@ __device__ ScoreOut score_candidate(const Ctx &c, const SearchParams &p, const M
             for (int g = 0; g < MAXT; ++g) tv[g] = (g == gx) ? tmx : ((g == gn) ? tmn : tv[g]);
         }
     }
-    float tmax = tv[0];
+    tmax = tv[0];
     {
         bool first = true;
         FOR_ACTIVE(g) { tmax = first ? tv[g] : fmaxf(tmax, tv[g]); first = false; }
@@ -667,8 +697,12 @@ __device__ ScoreOut score_candidate(const Ctx &c, const SearchParams &p, const M
         out.cost = ((p.gate == 1 && tmax > tmax_star) || (p.gate == 2 && tmax >= tmax_star)) ? __int_as_float(0x7f800000)
                                                                                               : 0.f;
         out.tmax = tmax;
+        out.amask = amask;
         return out;
     }
+    }   // STAGE != 2
+    const int di = (na - 1) * c.T;
+    const int g_first = __ffs(amask) - 1;
 
     // --- SU assignment (Algorithm 2, Eq. 6). R(g) is fixed now: one reciprocal per tour.
     {
@@ -912,11 +946,11 @@ __host__ __device__ inline size_t align16(size_t x) { return (x + 15) & ~size_t(
 
 struct SmemPlan {
     size_t off_blob, off_plan, off_derived, off_supq, off_bad, off_base_agg, off_tour, off_qidx, off_qmv, off_qidx2,
-        off_qmv2, total;
+        off_qmv2, off_surv, total;
 };
 
 __host__ __device__ inline SmemPlan carve(size_t tour_bytes, int threads, int max_prefix, int max_plan_len, int max_F,
-                                          int max_B, int max_T)
+                                          int max_B, int max_T, size_t surv_bytes = 0)
 {
     SmemPlan s;
     size_t o = 0;
@@ -932,6 +966,7 @@ __host__ __device__ inline SmemPlan carve(size_t tour_bytes, int threads, int ma
     s.off_qmv = o; o += align16((size_t)(threads / 32) * WQ * 8);
     s.off_qidx2 = o; o += align16((size_t)(threads / 32) * WQ * 4);   // candidates that passed the gate
     s.off_qmv2 = o; o += align16((size_t)(threads / 32) * WQ * 8);
+    s.off_surv = o; o += align16((size_t)(threads / 32) * WQ * surv_bytes);   // and their first-stage results
     s.total = o;
     return s;
 }
@@ -939,7 +974,8 @@ __host__ __device__ inline SmemPlan carve(size_t tour_bytes, int threads, int ma
 template <class SH>
 __host__ __device__ inline SmemPlan carve_shape(int max_prefix, int max_plan_len, int max_F, int max_B, int max_T)
 {
-    return carve(TourState<SH>::bytes(), SH::NT, max_prefix, max_plan_len, max_F, max_B, max_T);
+    return carve(TourState<SH>::bytes(), SH::NT, max_prefix, max_plan_len, max_F, max_B, max_T,
+                 kKeepSurvivors<SH> ? sizeof(Survivor<SH>) : 0);
 }
 
 struct BlockShared {
@@ -1266,6 +1302,7 @@ __global__ void __launch_bounds__(SH::NT, SH::MINB) search_iteration_kernel(cons
     int2 *qmv = (int2 *)(smem + sp.off_qmv) + warp * WQ;
     int32_t *qidx2 = (int32_t *)(smem + sp.off_qidx2) + warp * WQ;
     int2 *qmv2 = (int2 *)(smem + sp.off_qmv2) + warp * WQ;
+    Survivor<SH> *surv = (Survivor<SH> *)(smem + sp.off_surv) + warp * WQ;   // used where kKeepSurvivors
     Ctx c;
     for (int w = blockIdx.x; w < n_work; w += gridDim.x) {
         const WorkItem wi = work[w];
@@ -1325,17 +1362,17 @@ __global__ void __launch_bounds__(SH::NT, SH::MINB) search_iteration_kernel(cons
                 bool kept = false;
                 int i = 0;
                 int2 pm = make_int2(0, 0);
+                ScoreOut r1 = {0.f, 0.f, 0u};
                 if (lane < take) {
                     const int slot = (qhead + lane) & (WQ - 1);
                     i = qidx[slot];
                     pm = qmv[slot];
                     const MoveRec m = {pm.x & 0xffff, pm.x >> 16, pm.y & 0xffff, pm.y >> 16};
-                    const ScoreOut r = score_candidate<SH, false, false, 1>(c, prm, m, tmax_star, tstate, tid, nullptr,
-                                                                           nullptr, nullptr, nullptr, nullptr, nullptr,
-                                                                           nullptr);
-                    if (isinf(r.cost)) {   // discarded by the gate: C = +inf (Sec. 2.5)
-                        const unsigned long long k = make_key(r.cost, (uint32_t)i);
-                        if (k < best) { best = k; best_t = r.tmax; }
+                    r1 = score_candidate<SH, false, false, 1>(c, prm, m, tmax_star, tstate, tid, nullptr, nullptr, nullptr,
+                                                              nullptr, nullptr, nullptr, nullptr);
+                    if (isinf(r1.cost)) {   // discarded by the gate: C = +inf (Sec. 2.5)
+                        const unsigned long long k = make_key(r1.cost, (uint32_t)i);
+                        if (k < best) { best = k; best_t = r1.tmax; }
                     } else {
                         kept = true;
                     }
@@ -1345,6 +1382,20 @@ __global__ void __launch_bounds__(SH::NT, SH::MINB) search_iteration_kernel(cons
                     const int slot = (q2head + q2count + __popc(ball & ((1u << lane) - 1u))) & (WQ - 1);
                     qidx2[slot] = i;
                     qmv2[slot] = pm;
+                    if constexpr (kKeepSurvivors<SH>) {
+                        // this lane's first-stage results, from its own tour-state columns
+                        TourState<SH> ts;
+                        ts.bind(tstate, tid);
+                        Survivor<SH> &sv = surv[slot];
+#pragma unroll
+                        for (int g = 0; g < SH::MAXT; ++g)
+                            if ((r1.amask >> g) & 1u) {
+                                sv.lhu[g] = ts.LHU.get(g); sv.lsu[g] = ts.LSU.get(g); sv.db2[g] = ts.DB2.get(g);
+                                sv.rq[g] = ts.Rq.get(g); sv.hm[g] = ts.Hm.get(g);
+                            }
+                        sv.amask = r1.amask;
+                        sv.tmax = r1.tmax;
+                    }
                 }
                 q2count += __popc(ball);
                 __syncwarp();
@@ -1359,8 +1410,14 @@ __global__ void __launch_bounds__(SH::NT, SH::MINB) search_iteration_kernel(cons
                     const int i = qidx2[slot];
                     const int2 pm = qmv2[slot];
                     const MoveRec m = {pm.x & 0xffff, pm.x >> 16, pm.y & 0xffff, pm.y >> 16};
-                    const ScoreOut r = score_candidate<SH, false>(c, prm, m, tmax_star, tstate, tid, nullptr, nullptr,
-                                                                  nullptr, nullptr, nullptr, nullptr, nullptr);
+                    ScoreOut r;
+                    if constexpr (kKeepSurvivors<SH>)
+                        r = score_candidate<SH, false, false, 2>(c, prm, m, tmax_star, tstate, tid, nullptr, nullptr,
+                                                                 nullptr, nullptr, nullptr, nullptr, nullptr, nullptr,
+                                                                 nullptr, &surv[slot]);
+                    else
+                        r = score_candidate<SH, false>(c, prm, m, tmax_star, tstate, tid, nullptr, nullptr, nullptr,
+                                                       nullptr, nullptr, nullptr, nullptr);
                     const unsigned long long k = make_key(r.cost, (uint32_t)i);
                     if (k < best) { best = k; best_t = r.tmax; }
                 }
