@@ -553,11 +553,36 @@ int init_common(const bl_instance *insts, int32_t n_inst, const bl_params *param
         initial_plan(h->insts[(size_t)i]);
         build_blob(h->insts[(size_t)i]);
     }
-    const int shape = pick_shape(h->insts);
-    h->cfg.shape = shape;
-    h->cfg.threads = threads_of(shape);
+    int shape = pick_shape(h->insts);
     int maxT = 0;
     for (const HostInst &hi : h->insts) maxT = std::max(maxT, hi.T);
+    h->cfg.max_plan_len = h->cfg.max_F = h->cfg.max_B = h->cfg.max_T = 0;
+    for (const HostInst &hi : h->insts) {
+        h->cfg.max_plan_len = std::max(h->cfg.max_plan_len, hi.plan_len);
+        h->cfg.max_F = std::max(h->cfg.max_F, hi.F);
+        h->cfg.max_B = std::max(h->cfg.max_B, hi.B);
+        h->cfg.max_T = std::max(h->cfg.max_T, hi.T);
+    }
+    // shared memory of a shape for these instances; a shape that stages the distances
+    // but does not fit gives way to the one that reads them through L2
+    auto smem_of = [&](int sh, int32_t &prefix) {
+        prefix = 0;
+        for (const HostInst &hi : h->insts)
+            prefix = std::max(prefix, dist_in_smem(sh) ? hi.L.total_bytes : hi.L.prefix_bytes);
+        return shared_bytes(sh, threads_of(sh), prefix, h->cfg.max_plan_len, h->cfg.max_F, h->cfg.max_B,
+                            h->cfg.max_T);
+    };
+    const size_t smem_limit = 227 * 1024 - 2048;   // leave room for the static shared memory of the kernels
+    int32_t prefix = 0;
+    size_t smem = smem_of(shape, prefix);
+    if (smem > smem_limit && shape != SHAPE_T16_S128_GMEM) {
+        shape = SHAPE_T16_S128_GMEM;
+        smem = smem_of(shape, prefix);
+    }
+    h->cfg.shape = shape;
+    h->cfg.threads = threads_of(shape);
+    h->cfg.max_prefix = prefix;
+    h->cfg.smem = smem;
     h->cfg.lanes = params->lanes_per_cand <= 1 ? 1 : params->lanes_per_cand;
     if (h->cfg.lanes > 1 && (!coop_supported(shape, h->cfg.lanes) || h->cfg.lanes < maxT)) {
         g_error = "lanes_per_cand " + std::to_string(h->cfg.lanes) + " is not built for this shape or is below the "
@@ -571,18 +596,7 @@ int init_common(const bl_instance *insts, int32_t n_inst, const bl_params *param
             delete h;
             return BL_ETOO_LARGE;
         }
-    h->cfg.max_prefix = 0;
-    h->cfg.max_plan_len = h->cfg.max_F = h->cfg.max_B = h->cfg.max_T = 0;
-    for (const HostInst &hi : h->insts) {
-        h->cfg.max_prefix = std::max(h->cfg.max_prefix, dist_in_smem(shape) ? hi.L.total_bytes : hi.L.prefix_bytes);
-        h->cfg.max_plan_len = std::max(h->cfg.max_plan_len, hi.plan_len);
-        h->cfg.max_F = std::max(h->cfg.max_F, hi.F);
-        h->cfg.max_B = std::max(h->cfg.max_B, hi.B);
-        h->cfg.max_T = std::max(h->cfg.max_T, hi.T);
-    }
-    h->cfg.smem = shared_bytes(shape, h->cfg.threads, h->cfg.max_prefix, h->cfg.max_plan_len, h->cfg.max_F,
-                               h->cfg.max_B, h->cfg.max_T);
-    if (h->cfg.smem > 227 * 1024 - 2048) {   // leave room for the static shared memory of the kernels
+    if (h->cfg.smem > smem_limit) {
         g_error = "instance tables do not fit in shared memory";
         delete h;
         return BL_ETOO_LARGE;

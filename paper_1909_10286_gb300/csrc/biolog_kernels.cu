@@ -527,7 +527,7 @@ struct Survivor {
 };
 // kept for shapes of at most 4 tours, where the records fit next to two blocks per SM
 template <class SH>
-constexpr bool kKeepSurvivors = SH::MAXT <= 4;
+constexpr bool kKeepSurvivors = SH::MAXT <= 8;
 
 // Per-thread per-tour state: one shared-memory column per value. (Completion
 // and waiting times live in registers during the local minimisations; the

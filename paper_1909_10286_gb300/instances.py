@@ -149,6 +149,17 @@ def make_instance(workload: str, seed: int = 0) -> Instance:
     raise ValueError(f"unknown workload {workload!r}")
 
 
+def make_sized(F: int, B: int, T: int, H: int, S: int, seed: int = 0) -> Instance:
+    """An instance with the paper workload's value distributions at chosen sizes
+    (edge cases: instances near a kernel shape's limits)."""
+    rng = np.random.default_rng([0xB11, seed, F, B, T, H, S])
+    half = 25.0 * float(np.sqrt(F / 40.0))   # field density of the paper workload
+    area = rng.uniform(5.0, 80.0, size=F)
+    yld = np.clip(rng.normal(40.0, 5.0, size=F), 1.0, None)
+    return _finish(f"sized{F}x{B}x{T}x{H}x{S}", seed, rng, F, B, T, H, S, half, area, yld,
+                   1.5, 4.0, 18.0, 32.0, 30.0, 50.0, 40.0, 0.9)
+
+
 def make_batch(workload: str, seeds) -> list[Instance]:
     return [make_instance(workload, int(s)) for s in seeds]
 
