@@ -238,10 +238,62 @@ def oracle_throughput(inst, params_kw, n_cand, budget_s, threads, max_iters=50, 
 WORKLOAD_LEARNED = ("learned proposals on the paper-scale instance: per iteration 2^20 Philox moves featurised and "
                     "ranked by the MLP 64-256-256-256-1 (BF16, tensor cores), the 0.9*2^18 best plus ~10% random "
                     "moves scored exactly")
+WORKLOAD_SURROGATE = ("surrogate pre-filter on the large instance (300 fields, 20 BPs, 10 tours, 60 HUs, 120 SUs): "
+                      "per iteration 2^24 Philox moves featurised and scored by the MLP 64-256-256-256-1 (BF16, "
+                      "tensor cores), the best 1% scored exactly")
+RANKED = {
+    # config 4: ranked proposals on the paper-scale instance
+    "learned": dict(text=WORKLOAD_LEARNED, inst="paper", pool=1 << 20, keep=int(0.9 * (1 << 18)),
+                    rand=0.1 * (1 << 18), train_iters=12, train_steps=600, compare_iters=0),
+    # config 5: the surrogate scores 2^24 candidates, the top 1 % are scored exactly; plain exact search
+    # at equal wall time beside it
+    "surrogate": dict(text=WORKLOAD_SURROGATE, inst="large", pool=1 << 24, keep=(1 << 24) // 100, rand=0.0,
+                      train_iters=12, train_steps=1500, compare_iters=100),
+}
+
+
+def _equal_wall_time(inst, kw, net, pool, keep, rand_frac, iters):
+    """C* after `iters` ranked iterations from the initial plan, and C* of plain exact searches (2^24 and
+    2^20 candidates per iteration) from the same plan given the same device time."""
+    import torch
+
+    from paper_1909_10286_gb300 import biolog
+
+    def timed(S, step, k):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(S.stream)
+        step(k)
+        b.record(S.stream)
+        b.synchronize()
+        return a.elapsed_time(b)
+
+    S = biolog.Search([inst], biolog.make_params(n_cand=pool, **kw))
+    netS = net.copy(stream=S.stream, max_batch=8192)
+    wall = timed(S, lambda k: S.search_step_learned(netS, k, pool, keep, rand_frac), iters)
+    out = {"device_ms": wall, "ranked": {"iters": iters, "cstar": S.get_state()["cstar"]}}
+    netS.close()
+    S.close()
+    for n in (1 << 24, 1 << 20):
+        # iterations in chunks until the device time reaches the ranked run's; C* after the same
+        # number of iterations as the ranked run is kept too (quality per iteration)
+        P = biolog.Search([inst], biolog.make_params(n_cand=n, **kw))
+        ms, k, c_at = 0.0, 0, None
+        while ms < wall:
+            step = max(1, min(iters, int((wall - ms) / max(ms / k, 1e-3) / 2) if k else 2))
+            if k < iters < k + step:
+                step = iters - k
+            ms += timed(P, P.search_step, step)
+            k += step
+            if k == iters:
+                c_at = P.get_state()["cstar"]
+        out[f"plain_2^{n.bit_length() - 1}"] = {"iters": k, "device_ms": ms, "cstar": P.get_state()["cstar"],
+                                               f"cstar_after_{iters}_iters": c_at}
+        P.close()
+    return out
 
 
 def run_learned(args, ws, rank, local):
-    """Config-4 form: ranked proposals. value = exactly scored candidates/s; the
+    """Configs 4 and 5: ranked proposals. value = exactly scored candidates/s; the
     roofline is the fused MLP forward's (the dominant kernel), timed on its own
     with CUDA events on the same pool of features."""
     import numpy as np
@@ -250,17 +302,20 @@ def run_learned(args, ws, rank, local):
     from paper_1909_10286_gb300 import biolog, learned
     from paper_1909_10286_gb300 import instances as I
 
+    spec = RANKED[args.workload]
     torch.cuda.set_device(local)
-    pool, keep = 1 << 20, int(0.9 * (1 << 18))
-    rand_frac = 0.1 * (1 << 18) / (pool - keep)
+    pool, keep = spec["pool"], spec["keep"]
+    rand_frac = spec["rand"] / (pool - keep)
     t0 = time.time()
-    X, T = learned.collect(I.make_batch("paper", range(100 + 10 * rank, 104 + 10 * rank)), iters=12, sample=8192)
-    net0, losses = learned.train(X, T, hidden=256, steps=600, batch=4096, lr=1e-3, max_batch=8192)
+    X, T = learned.collect(I.make_batch(spec["inst"], range(100 + 10 * rank, 104 + 10 * rank)),
+                           iters=spec["train_iters"], sample=8192)
+    net0, losses = learned.train(X, T, hidden=256, steps=spec["train_steps"], batch=4096, lr=1e-3, max_batch=8192)
     t_train = time.time() - t0
-    inst = I.make_instance("paper", args.seed + rank)
-    S = biolog.Search([inst], biolog.make_params(n_cand=pool, eps=0.5, seed=1000 + args.seed + rank, gate=1))
-    net = net0.copy(stream=S.stream, max_batch=pool)
-    net0.close()
+    inst = I.make_instance(spec["inst"], args.seed + rank)
+    kw = dict(eps=0.5, seed=1000 + args.seed + rank, gate=1)
+    S = biolog.Search([inst], biolog.make_params(n_cand=pool, **kw))
+    # the fused forward takes any number of rows; max_batch only sizes the training buffers
+    net = net0.copy(stream=S.stream, max_batch=8192)
     stream = S.stream
     S.search_step_learned(net, args.warmup, pool, keep, rand_frac)
     torch.cuda.synchronize()
@@ -283,7 +338,6 @@ def run_learned(args, ws, rank, local):
     ms_step = t_ms / args.steps
     # exactly scored candidates per iteration: the kept list (its length is data dependent)
     feat = torch.empty((pool, 64), dtype=torch.bfloat16, device="cuda")
-    st = S.get_state()
     S.features(-1, 0xFFFFFFFF, 0, pool, feat)
     y = torch.empty(pool, dtype=torch.float32, device="cuda")
     with torch.cuda.stream(stream):
@@ -293,6 +347,7 @@ def run_learned(args, ws, rank, local):
     sample = np.sort(yv[(np.arange(4096) * pool) // 4096])
     th = sample[min(4095, keep * 4096 // pool)]
     n_exact = int((yv <= th).sum()) + int(round(rand_frac * int((yv > th).sum())))
+    del yv
     value = n_exact * args.steps * ws / (t_ms / 1e3)
     # the fused MLP forward alone, on the same features, timed with CUDA events on its stream
     fe = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(5)]
@@ -304,6 +359,7 @@ def run_learned(args, ws, rank, local):
         b.record(stream)
     torch.cuda.synchronize()
     ms_mlp = statistics.median(a.elapsed_time(b) for a, b in fe)
+    del feat, y
     flop = 2.0 * (64 * 256 + 2 * 256 * 256 + 256) * pool
     peaks = _peaks()
     peak = float(peaks.get("bf16_tflops", 1900.0))
@@ -311,10 +367,11 @@ def run_learned(args, ws, rank, local):
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f32 scorer, bf16 ranker", "data": "synthetic",
-            "config": {"workload": WORKLOAD_LEARNED, "instance_seed": args.seed, "pool": pool, "keep": keep,
+            "config": {"workload": spec["text"], "instance_seed": args.seed, "pool": pool, "keep": keep,
                        "rand_frac": rand_frac, "exact_per_iter": n_exact,
                        "l2": "flushed before every timed step (256 MiB device write)",
-                       "ranker_training": {"tuples": int(X.shape[0]), "steps": 600, "s": round(t_train, 1)},
+                       "ranker_training": {"tuples": int(X.shape[0]), "steps": spec["train_steps"],
+                                           "s": round(t_train, 1)},
                        "kernel": S.config(), "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU"},
             "proposals_per_s": pool * args.steps * ws / (t_ms / 1e3),
             "gpu_launches": args.steps * 5, "clocks": clk,
@@ -323,10 +380,13 @@ def run_learned(args, ws, rank, local):
                          "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None, "ms_per_launch": ms_mlp,
                          "flop_per_launch": flop,
                          "peak_basis": "bf16_tflops (burst) of MEASURED_PEAKS.json; kernel timed alone"}}
-    if rank == 0:
-        print(json.dumps(line), flush=True)
     net.close()
     S.close()
+    if spec["compare_iters"] and rank == 0:
+        line["equal_wall_time"] = _equal_wall_time(inst, kw, net0, pool, keep, rand_frac, spec["compare_iters"])
+    net0.close()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
 
 
 def rank_instances(workload: str, seed: int, rank: int, n_inst: int):
@@ -396,7 +456,7 @@ def main():
     if args.impl == "reference":
         run_reference(args, ws, rank)
         return
-    if args.workload == "learned":
+    if args.workload in RANKED:
         run_learned(args, ws, rank, local)
         return
     if args.study:

@@ -525,7 +525,7 @@ struct Survivor {
     unsigned amask;
     float tmax;
 };
-// kept for shapes of at most 4 tours, where the records fit next to two blocks per SM
+// kept for shapes of at most 8 tours, where the records fit in shared memory next to the rest
 template <class SH>
 constexpr bool kKeepSurvivors = SH::MAXT <= 8;
 
@@ -986,6 +986,7 @@ struct BlockShared {
     int32_t last;
     int32_t use_best;
     uint32_t iter;
+    int32_t cursor;   // next undrawn candidate position of the work item (chunks of 32)
     float base_cost;
     float base_tc[16];
     unsigned long long red[32];
@@ -1128,34 +1129,68 @@ __device__ bool stage_base(const InstMeta &M, BlockShared &bs, unsigned char *sm
     return true;
 }
 
-// stage_base, then the base plan's own per-tour T_compl, shuttle ratio and
-// shuttle sum, scored by thread 0 with the candidates' code.
+// The base plan's own per-tour T_compl, shuttle ratio and shuttle sum (the
+// shuttle memo of the candidates' scoring), scored by the calling thread with
+// the candidates' code; c.memo must still be 0.
+template <class SH>
+__device__ __forceinline__ void score_base(const InstMeta &M, BlockShared &bs, unsigned char *smem, const SmemPlan &sp,
+                                        const SearchParams &p, Ctx &c)
+{
+    const int T = M.T;
+    float *kf_base = const_cast<float *>(c.kf_base);
+    long long *sh_base = const_cast<long long *>(c.sh_base);
+    c.nbad = bs.nbad;
+    for (int g = 0; g < T; ++g) { kf_base[g] = 0.f; sh_base[g] = 0; }
+    bs.base_cost = __int_as_float(0x7f800000);
+    for (int g = 0; g < T && g < 16; ++g) bs.base_tc[g] = 0.f;
+    if (bs.nbad == 0) {
+        const MoveRec idm = {4, 0, 0, 0};
+        bs.base_cost = score_candidate<SH, false, true>(c, p, idm, __int_as_float(0x7f800000), smem + sp.off_tour,
+                                                        threadIdx.x, nullptr, nullptr, bs.base_tc, nullptr, nullptr,
+                                                        nullptr, nullptr, kf_base, sh_base)
+                           .cost;
+    }
+}
+
+// stage_base, then the base plan scored by thread 0 (score_base).
 template <class SH>
 __device__ bool stage_instance(const InstMeta &M, BlockShared &bs, unsigned char *smem, const SmemPlan &sp,
                                const SearchParams &p, int use_best_override, uint32_t iter_override, Ctx &c)
 {
     if (!stage_base<SH>(M, bs, smem, sp, p, use_best_override, iter_override, c)) return false;
-    const int tid = threadIdx.x, T = M.T;
-    float *kf_base = const_cast<float *>(c.kf_base);
-    long long *sh_base = const_cast<long long *>(c.sh_base);
-    if (tid == 0) {
-        c.nbad = bs.nbad;
-        for (int g = 0; g < T; ++g) { kf_base[g] = 0.f; sh_base[g] = 0; }
-        bs.base_cost = __int_as_float(0x7f800000);
-        for (int g = 0; g < T && g < 16; ++g) bs.base_tc[g] = 0.f;
-        if (bs.nbad == 0) {
-            // the base plan's T_compl, shuttle ratio N_SU / sum cap and exact shuttle sum of every active tour
-            const MoveRec idm = {4, 0, 0, 0};
-            bs.base_cost = score_candidate<SH, false, true>(c, p, idm, __int_as_float(0x7f800000), smem + sp.off_tour,
-                                                            tid, nullptr, nullptr, bs.base_tc, nullptr, nullptr,
-                                                            nullptr, nullptr, kf_base, sh_base)
-                               .cost;
-        }
-    }
+    if (threadIdx.x == 0) score_base<SH>(M, bs, smem, sp, p, c);
     __syncthreads();
     c.nbad = bs.nbad;
     c.memo = 1;
     return true;
+}
+
+// Whether the search kernel scores the base plan in warp 0 while the other
+// warps start on the candidates: not in shape B, whose register budget (128 at
+// 4 blocks per SM) does not hold the base scoring next to the candidate loop.
+template <class SH>
+constexpr bool kOverlapBase = SH::MAXT != 8;
+
+// Named barrier 1 (barrier 0 is __syncthreads): the producer warp arrives
+// without waiting, the consumer warps wait until all `n` threads have arrived.
+__device__ __forceinline__ void named_arrive(int n)
+{
+    asm volatile("bar.arrive 1, %0;" ::"r"(n) : "memory");
+}
+__device__ __forceinline__ void named_sync(int n)
+{
+    asm volatile("bar.sync 1, %0;" ::"r"(n) : "memory");
+}
+
+// List mode: an instance's kept candidates are dealt to as many of its work
+// items as the grid runs side by side (about one per block), a multiple of 32
+// each; its remaining work items are empty and only report an empty slot.
+__device__ __forceinline__ int list_tile(const InstMeta &M, int list_n, int n_work)
+{
+    const int n = min(M.n_cand, list_n);
+    const long long share = (long long)M.n_tiles * gridDim.x / (n_work > 0 ? n_work : 1);
+    const int items = (int)(share < 1 ? 1 : (share < M.n_tiles ? share : M.n_tiles));
+    return max(32, ((n + items - 1) / items + 31) & ~31);
 }
 
 __device__ __forceinline__ unsigned long long make_key(float cost, uint32_t i)
@@ -1307,21 +1342,28 @@ __global__ void __launch_bounds__(SH::NT, SH::MINB) search_iteration_kernel(cons
     for (int w = blockIdx.x; w < n_work; w += gridDim.x) {
         const WorkItem wi = work[w];
         const InstMeta &M = meta[wi.inst];
-        if (bs.staged != wi.inst) {
-            if (!stage_instance<SH>(M, bs, smem, sp, prm, -1, 0xffffffffu, c)) return;
+        const bool fresh_inst = bs.staged != wi.inst;
+        if (fresh_inst) {
+            if constexpr (kOverlapBase<SH>) {
+                if (!stage_base<SH>(M, bs, smem, sp, prm, -1, 0xffffffffu, c)) return;
+            } else {
+                if (!stage_instance<SH>(M, bs, smem, sp, prm, -1, 0xffffffffu, c)) return;
+            }
             if (tid == 0) bs.staged = wi.inst;
-            __syncthreads();
         }
         const float tmax_star = M.state->tmaxstar;
         const uint32_t iter = bs.iter;
         // list mode (learned proposals): positions index instance wi.inst's list of candidate numbers
         const int list_n = cand_list ? cand_count[wi.inst] : 0;
         const uint32_t *ilist = cand_list ? cand_list + (size_t)wi.inst * list_stride : nullptr;
-        // list mode: the kept candidates are dealt evenly over the instance's work items
-        // (a multiple of 32 each), whatever the tile the full pool was planned with
-        const int tl = cand_list ? max(32, ((min(M.n_cand, list_n) + M.n_tiles - 1) / M.n_tiles + 31) & ~31) : M.tile;
-        const int c0 = wi.tile_idx * tl;
-        const int c1 = min(c0 + tl, cand_list ? min(M.n_cand, list_n) : M.n_cand);
+        // list mode: the kept candidates go to about one work item per block (list_tile),
+        // whatever the tile the full pool was planned with
+        const int tl = cand_list ? list_tile(M, list_n, n_work) : M.tile;
+        // positions [c0, c1) of the instance's candidates (or of its list); empty past the end
+        const long long cend = cand_list ? min(M.n_cand, list_n) : M.n_cand;
+        const long long c0l = (long long)wi.tile_idx * tl;
+        const int c0 = (int)min(c0l, cend);
+        const int c1 = (int)min(c0l + tl, cend);
         unsigned long long best = ~0ull;
         float best_t = 0.f;
         // each warp: draw 32 moves at a time and queue the feasible ones (Eq. 2); take 32 queued
@@ -1329,10 +1371,31 @@ __global__ void __launch_bounds__(SH::NT, SH::MINB) search_iteration_kernel(cons
         // those at a time in full. The gate discards most feasible candidates: their cost is
         // +inf once Tmax is known, and the SU assignment and shuttle pass run in full warps
         // of the others only.
+        // Warps take chunks of 32 positions from a block-wide cursor, so a warp whose candidates
+        // ran through the gate quickly draws more and all warps run out of draws together.
         int qhead = 0, qcount = 0;     // warp-uniform ring-buffer state, feasible candidates
         int q2head = 0, q2count = 0;   // candidates the gate kept
-        for (int base = c0 + warp * 32; base < c1 || qcount > 0 || q2count > 0; base += NT) {
-            // (c1 may be below c0 in list mode: then the work item only reports an empty slot)
+        if (tid == 0) bs.cursor = c0 + NT;
+        __syncthreads();
+        // A freshly staged instance: warp 0 scores the base plan (the shuttle memo) while the
+        // other warps draw and take candidates to the gate; they wait for it (named barrier 1)
+        // before their first full score, or at the end if they have none.
+        bool memo_wait = false;
+        if (kOverlapBase<SH> && fresh_inst) {
+            if (warp == 0) {
+                if (lane == 0) score_base<SH>(M, bs, smem, sp, prm, c);
+                __syncwarp();
+                __threadfence_block();
+                named_arrive(NT);
+            } else {
+                memo_wait = true;
+            }
+            c.nbad = bs.nbad;
+            c.memo = 1;
+        }
+        for (int base = c0 + warp * 32;;) {
+            // (an empty range, past the end of a list, only reports an empty slot)
+            int next = c1;   // this warp's next chunk
             if (base < c1) {
                 const int pos = base + lane;
                 const int i = (ilist && pos < c1) ? (int)ilist[pos] : pos;
@@ -1354,8 +1417,11 @@ __global__ void __launch_bounds__(SH::NT, SH::MINB) search_iteration_kernel(cons
                 }
                 qcount += __popc(ball);
                 __syncwarp();
+                int nb = 0;
+                if (lane == 0) nb = atomicAdd(&bs.cursor, 32);
+                next = __shfl_sync(0xffffffffu, nb, 0);
             }
-            const bool drained = base + NT >= c1;   // no more draws
+            const bool drained = next >= c1;   // no more draws for this warp
             // up to the gate for a full warp of feasible candidates, or the remainder once drained
             const int take = (qcount >= 32) ? 32 : (drained ? qcount : 0);
             if (take > 0) {
@@ -1405,6 +1471,7 @@ __global__ void __launch_bounds__(SH::NT, SH::MINB) search_iteration_kernel(cons
             // the full score of a warp of candidates the gate kept, or the remainder at the end
             const int take2 = (q2count >= 32) ? 32 : ((drained && qcount == 0) ? q2count : 0);
             if (take2 > 0) {
+                if (memo_wait) { named_sync(NT); memo_wait = false; }
                 if (lane < take2) {
                     const int slot = (q2head + lane) & (WQ - 1);
                     const int i = qidx2[slot];
@@ -1425,6 +1492,11 @@ __global__ void __launch_bounds__(SH::NT, SH::MINB) search_iteration_kernel(cons
                 q2head = (q2head + take2) & (WQ - 1);
                 q2count -= take2;
             }
+            if (drained && qcount == 0 && q2count == 0) {
+                if (memo_wait) { named_sync(NT); memo_wait = false; }
+                break;
+            }
+            base = next;
         }
         block_argmin_finalize<NT>(best, best_t, bs, M, wi, slot_key, slot_tmax, slot_base, c, prm, iter);
     }
@@ -1921,9 +1993,12 @@ __global__ void __launch_bounds__(COOP_NT) search_iteration_coop_kernel(
         const uint32_t iter = bs.iter;
         const int list_n = cand_list ? cand_count[wi.inst] : 0;
         const uint32_t *ilist = cand_list ? cand_list + (size_t)wi.inst * list_stride : nullptr;
-        const int tl = cand_list ? max(32, ((min(M.n_cand, list_n) + M.n_tiles - 1) / M.n_tiles + 31) & ~31) : M.tile;
-        const int c0 = wi.tile_idx * tl;
-        const int c1 = min(c0 + tl, cand_list ? min(M.n_cand, list_n) : M.n_cand);
+        const int tl = cand_list ? list_tile(M, list_n, n_work) : M.tile;
+        // positions [c0, c1) of the instance's candidates (or of its list); empty past the end
+        const long long cend = cand_list ? min(M.n_cand, list_n) : M.n_cand;
+        const long long c0l = (long long)wi.tile_idx * tl;
+        const int c0 = (int)min(c0l, cend);
+        const int c1 = (int)min(c0l + tl, cend);
         unsigned long long best = ~0ull;
         float best_t = 0.f;
         for (int pos = c0 + grp; pos < c1; pos += NG) {

@@ -251,8 +251,10 @@ gemm_bf16_tn_kernel(const __nv_bfloat16 *__restrict__ A, const __nv_bfloat16 *__
 //   rg, k block kb) at kb * 2048 + rg * 128 bytes   -> LBO 2048, SBO 128
 //   weight chunk: core matrix (n group ng, k block kb) at kb * (H * 16) + ng * 128
 //                                                      -> LBO H * 16, SBO 128
-// Warp w (8 warps) reads TMEM lanes 32 (w % 4) .. +31 and the column half w / 4.
-constexpr int FTHREADS = 256;
+// Epilogue: warp w (16 warps) reads TMEM lanes 32 (w % 4) .. +31 of tile
+// (w / 4) % 2, columns of half w / 8; four warps per scheduler hide the
+// latency of the TMEM loads and shared stores of one another.
+constexpr int FTHREADS = 512;
 constexpr int FKMAX = 64;   // largest K per weight chunk
 
 // Weight chunking: a bulk copy costs about the same time whatever its size up
@@ -345,15 +347,16 @@ __device__ __forceinline__ void pin16(uint32_t *v)
     asm volatile("" : "+r"(v[0]), "+r"(v[1]), "+r"(v[2]), "+r"(v[3]), "+r"(v[4]), "+r"(v[5]), "+r"(v[6]), "+r"(v[7]),
                  "+r"(v[8]), "+r"(v[9]), "+r"(v[10]), "+r"(v[11]), "+r"(v[12]), "+r"(v[13]), "+r"(v[14]), "+r"(v[15]));
 }
-// 16 * nb accumulator columns from c0 (nb <= 4) with a single wait
+// 16 * nb accumulator columns from c0 (nb <= NB) with a single wait
+template <int NB>
 __device__ __forceinline__ void tmem_ld_group(uint32_t taddr, int nb, uint32_t (*v)[16])
 {
 #pragma unroll
-    for (int b = 0; b < 4; ++b)
+    for (int b = 0; b < NB; ++b)
         if (b < nb) tmem_ld16_nowait(taddr + 16u * b, v[b]);
     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
-    for (int b = 0; b < 4; ++b)
+    for (int b = 0; b < NB; ++b)
         if (b < nb) pin16(v[b]);
 }
 
@@ -437,6 +440,7 @@ fused_mlp_forward_kernel(const __nv_bfloat16 *__restrict__ X, int M, int I, int 
     __shared__ uint64_t tma_bar[4], mma_bar[4], layer_bar, drain_bar;
     __shared__ uint32_t tmem_base_sh;
     __shared__ int fail_sh;
+    __shared__ float ypart[2][256];   // output layer: the two column halves' dot products per row
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const FusedGeom G = fused_geom(I, H);
     const int nch1 = G.nch1, nch2 = G.nch2, cpt = G.cpt;
@@ -526,17 +530,46 @@ fused_mlp_forward_kernel(const __nv_bfloat16 *__restrict__ X, int M, int I, int 
 
     if (tid == 0)
         while (loaded < total && loaded < nbuf) load_chunk(loaded++);
-    // epilogue roles: warp w reads TMEM lanes 32 (w % 4) .. +31 of tile w / 4
-    const int q = warp & 3, t_ep = warp >> 2;
+    // epilogue roles: warp w reads TMEM lanes 32 (w % 4) .. +31 of tile (w / 4) % 2, column half w / 8
+    const int q = warp & 3, t_ep = (warp >> 2) & 1, half = warp >> 3;
     const int row_in_tile = 32 * q + lane;
+    const int col_lo = half * (H / 2), col_hi = col_lo + H / 2;   // H / 2 is a multiple of 16
+    // The next pair's inputs are loaded into registers while the last layer's MMAs run
+    // (16-byte rows, at most XPRE segments per thread); other widths are staged directly.
+    constexpr int XPRE = 4;
+    const int xsegs = 128 * G.xkb;   // 16-byte segments per tile
+    const bool xpre = (I % 8) == 0 && (reinterpret_cast<uintptr_t>(X) & 15) == 0 && 2 * xsegs <= XPRE * FTHREADS;
+    uint4 xr[XPRE];
+    auto x_load = [&](int pair) {
+#pragma unroll
+        for (int k = 0; k < XPRE; ++k) {
+            const int s = tid + k * FTHREADS, t = s >= xsegs ? 1 : 0, s2 = s - t * xsegs;
+            const int row = (2 * pair + t) * 128 + (s2 & 127), kk = (s2 >> 7) * 8;
+            xr[k] = (s < 2 * xsegs && row < M && kk < I) ? __ldg(reinterpret_cast<const uint4 *>(X + (size_t)row * I + kk))
+                                                       : make_uint4(0u, 0u, 0u, 0u);
+        }
+    };
+    auto x_store = [&]() {
+#pragma unroll
+        for (int k = 0; k < XPRE; ++k) {
+            const int s = tid + k * FTHREADS, t = s >= xsegs ? 1 : 0, s2 = s - t * xsegs;
+            const int r = s2 & 127;
+            if (s < 2 * xsegs)
+                *reinterpret_cast<uint4 *>(act[t] + (s2 >> 7) * 2048 + (r >> 3) * 128 + (r & 7) * 16) = xr[k];
+        }
+    };
     uint32_t layer_ph = 0;
     bool ok = true;
     for (int p = 0; p < my_pairs && ok; ++p) {
         const int pair = (int)blockIdx.x + p * (int)gridDim.x;
         // both tiles' inputs into their activation buffers (the last layer's MMAs of the
         // previous pair, the readers of these buffers, completed before its epilogue)
-        fused_stage_x(act[0], X, M, I, G.xkb, (2 * pair) * 128, tid, FTHREADS);
-        fused_stage_x(act[1], X, M, I, G.xkb, (2 * pair + 1) * 128, tid, FTHREADS);
+        if (xpre && p > 0) {
+            x_store();
+        } else {
+            fused_stage_x(act[0], X, M, I, G.xkb, (2 * pair) * 128, tid, FTHREADS);
+            fused_stage_x(act[1], X, M, I, G.xkb, (2 * pair + 1) * 128, tid, FTHREADS);
+        }
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         __syncthreads();
         for (int layer = 0; layer < 3 && ok; ++layer) {
@@ -548,6 +581,7 @@ fused_mlp_forward_kernel(const __nv_bfloat16 *__restrict__ X, int M, int I, int 
                 if (good) tc_commit(&layer_bar);
                 else fail_sh = 1;
             }
+            if (layer == 2 && xpre && p + 1 < my_pairs) x_load(pair + (int)gridDim.x);
             __syncwarp();
             const bool got = (volatile int &)fail_sh == 0 && mbar_wait(&layer_bar, layer_ph);
             layer_ph ^= 1u;
@@ -558,12 +592,12 @@ fused_mlp_forward_kernel(const __nv_bfloat16 *__restrict__ X, int M, int I, int 
             const float *bias = par + layer * H;
             if (layer < 2) {
                 unsigned char *dst0 = act[t_ep] + (row_in_tile >> 3) * 128 + (row_in_tile & 7) * 16;
-                for (int c0 = 0; c0 < H; c0 += 64) {
-                    const int nb = min(4, (H - c0) / 16);
-                    uint32_t v[4][16];
-                    tmem_ld_group(taddr + (uint32_t)c0, nb, v);
+                for (int c0 = col_lo; c0 < col_hi; c0 += 32) {
+                    const int nb = min(2, (col_hi - c0) / 16);
+                    uint32_t v[2][16];
+                    tmem_ld_group<2>(taddr + (uint32_t)c0, nb, v);
 #pragma unroll
-                    for (int b = 0; b < 4; ++b) {
+                    for (int b = 0; b < 2; ++b) {
                         if (b >= nb) break;
                         const int cb = c0 + 16 * b;
                         const float4 *b4v = reinterpret_cast<const float4 *>(bias + cb);
@@ -585,12 +619,12 @@ fused_mlp_forward_kernel(const __nv_bfloat16 *__restrict__ X, int M, int I, int 
             } else {
                 float acc = 0.f;
                 const float *wv = par + 3 * H;
-                for (int c0 = 0; c0 < H; c0 += 64) {
-                    const int nb = min(4, (H - c0) / 16);
-                    uint32_t v[4][16];
-                    tmem_ld_group(taddr + (uint32_t)c0, nb, v);
+                for (int c0 = col_lo; c0 < col_hi; c0 += 32) {
+                    const int nb = min(2, (col_hi - c0) / 16);
+                    uint32_t v[2][16];
+                    tmem_ld_group<2>(taddr + (uint32_t)c0, nb, v);
 #pragma unroll
-                    for (int b = 0; b < 4; ++b) {
+                    for (int b = 0; b < 2; ++b) {
                         if (b >= nb) break;
                         const int cb = c0 + 16 * b;
 #pragma unroll
@@ -601,8 +635,10 @@ fused_mlp_forward_kernel(const __nv_bfloat16 *__restrict__ X, int M, int I, int 
                         }
                     }
                 }
+                ypart[half][t_ep * 128 + row_in_tile] = acc;
+                __syncthreads();
                 const int row = (2 * pair + t_ep) * 128 + row_in_tile;
-                if (row < M) y[row] = acc + par[4 * H];
+                if (half == 0 && row < M) y[row] = (acc + ypart[1][t_ep * 128 + row_in_tile]) + par[4 * H];
             }
             asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
             __syncthreads();
