@@ -89,6 +89,16 @@ __device__ __forceinline__ uint4 pack8_bf16(const float *x)
     return make_uint4(w[0], w[1], w[2], w[3]);
 }
 
+// max(x, 0) rounded to BF16 for a pair (lo, hi), packed lo | hi << 16: one cvt with
+// ReLU (rounding is monotonic and keeps 0, so it equals rounding max(x, 0); a NaN
+// stays NaN, where fmaxf would give 0)
+__device__ __forceinline__ uint32_t relu_bf16x2(float lo, float hi)
+{
+    uint32_t w;
+    asm("cvt.rn.relu.bf16x2.f32 %0, %1, %2;" : "=r"(w) : "f"(hi), "f"(lo));
+    return w;
+}
+
 // Copy a [rows x 64] BF16 chunk (row stride ld elements, starting at column k0)
 // into 4 slabs of 16 K each; rows >= nrows and columns >= K are zero.
 __device__ __forceinline__ void stage_chunk(__nv_bfloat16 *dst, const __nv_bfloat16 *src, int rows, int nrows, int ld,
@@ -440,24 +450,24 @@ fused_mlp_forward_kernel(const __nv_bfloat16 *__restrict__ X, int M, int I, int 
     __shared__ uint64_t tma_bar[4], mma_bar[4], layer_bar, drain_bar;
     __shared__ uint32_t tmem_base_sh;
     __shared__ int fail_sh;
-    __shared__ float ypart[2][256];   // output layer: the two column halves' dot products per row
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const FusedGeom G = fused_geom(I, H);
     const int nch1 = G.nch1, nch2 = G.nch2, cpt = G.cpt;
     const FusedSmem L = fused_smem(I, H, nbuf);
-    unsigned char *act[2] = {smem + L.act0, smem + L.act1};
+    // the two tiles' activation buffers: act_of(t) (no pointer array: it would live in local memory)
+    auto act_of = [&](int t) { return smem + (t ? L.act1 : L.act0); };
     unsigned char *wb = smem + L.wb;
     float *par = reinterpret_cast<float *>(smem + L.par);   // b1 | b2 | b3 | w4 | b4
+    for (int i = tid; i < H; i += FTHREADS) {
+        par[i] = b1[i]; par[H + i] = b2[i]; par[2 * H + i] = b3[i]; par[3 * H + i] = w4[i];
+    }
+    if (tid == 0) par[4 * H] = b4[0];
     const uint32_t buf_bytes = (uint32_t)G.max_chunk_bytes;   // ring buffer stride
     const int ntiles = (M + 127) / 128;
     const int npairs = (ntiles + 1) / 2;
     const int my_pairs = blockIdx.x < npairs ? (npairs - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
     const long long total = (long long)my_pairs * cpt;   // weight chunks this CTA consumes
 
-    for (int i = tid; i < H; i += FTHREADS) {
-        par[i] = b1[i]; par[H + i] = b2[i]; par[2 * H + i] = b3[i]; par[3 * H + i] = w4[i];
-    }
-    if (tid == 0) par[4 * H] = b4[0];
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base_sh)),
                      "r"(2 * TMEM_COLS)
@@ -481,55 +491,65 @@ fused_mlp_forward_kernel(const __nv_bfloat16 *__restrict__ X, int M, int I, int 
     const uint32_t idesc = instr_desc(128, H);
 
     // producer state (thread 0): chunks are loaded nbuf ahead; each barrier's
-    // completions are waited on in order, so one parity bit per barrier suffices
+    // completions are waited on in order, so one parity bit per barrier suffices.
+    // Ring slots and chunk numbers advance by counters (no 64-bit division between MMAs).
     long long loaded = 0;        // chunks whose bulk copy was issued
     long long consumed = 0;      // chunks whose MMAs were issued
+    int lb = 0, lj = 0;          // ring slot and chunk-in-pair of the next load
+    int cb = 0, cj = 0;          // ring slot and chunk-in-pair of the next chunk to consume
     uint32_t tma_ph = 0, mma_ph = 0;   // bit b: parity of the next wait on buffer b
-    auto load_chunk = [&](long long j) {
-        const int b = (int)(j % nbuf);
+    // descriptors: the start-address field (bits 0-13, address >> 4) is added per operand
+    const uint64_t a_tmpl = smem_desc(smem, 2048, 128) & ~0x3FFFull;
+    const uint64_t b_tmpl = smem_desc(smem, (uint32_t)H * 16, 128) & ~0x3FFFull;
+    const uint32_t a_addr0 = smem_u32(smem + L.act0) >> 4, a_addr1 = smem_u32(smem + L.act1) >> 4;
+    const uint32_t w_addr = smem_u32(wb) >> 4;
+    auto load_chunk = [&]() {
         int layer, c, kc;
         size_t off;
-        fused_chunk(G, H, (int)(j % cpt), layer, c, kc, off);
+        fused_chunk(G, H, lj, layer, c, kc, off);
         const uint32_t bytes = (uint32_t)H * kc * 2;
-        mbar_expect_tx_bytes(&tma_bar[b], bytes);
-        bulk_g2s(wb + (size_t)b * buf_bytes, wpack + off / 16, bytes, &tma_bar[b]);
+        mbar_expect_tx_bytes(&tma_bar[lb], bytes);
+        bulk_g2s(wb + (size_t)lb * buf_bytes, wpack + off / 16, bytes, &tma_bar[lb]);
+        ++loaded;
+        lb = lb + 1 == nbuf ? 0 : lb + 1;
+        lj = lj + 1 == cpt ? 0 : lj + 1;
     };
     // issue the MMAs of the next chunk for both tiles; false if a bounded wait gave up
     auto consume_chunk = [&]() -> bool {
-        const long long j = consumed;
-        const int b = (int)(j % nbuf);
+        const int b = cb;
         if (!mbar_wait(&tma_bar[b], (tma_ph >> b) & 1u)) return false;
         tma_ph ^= 1u << b;
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         int layer, c, kc;
         size_t off;
-        fused_chunk(G, H, (int)(j % cpt), layer, c, kc, off);
+        fused_chunk(G, H, cj, layer, c, kc, off);
         const int K = layer == 0 ? I : H;
-        const unsigned char *B = wb + (size_t)b * buf_bytes;
-        for (int s = 0; s < kc / 16; ++s) {
+        const uint32_t bsl = w_addr + (uint32_t)(b * (buf_bytes >> 4));
+        const int ns = (min(kc, K - c * kc) + 15) / 16;   // K steps of 16 in this chunk (zero padded past K)
+        for (int s = 0; s < ns; ++s) {
             const int k = c * kc + s * 16;
-            if (k >= K) break;
-            const uint64_t bd = smem_desc(B + (size_t)(2 * s) * H * 16, (uint32_t)H * 16, 128);
+            const uint64_t bd = b_tmpl | (uint64_t)(bsl + (uint32_t)(2 * s * H));   // (2 s H 16) >> 4
+            const uint32_t ko = (uint32_t)(k / 8) * (2048 >> 4);
             const uint32_t acc = (c > 0 || s > 0) ? 1u : 0u;
-#pragma unroll
-            for (int t = 0; t < 2; ++t)
-                tc_mma(tmem + (uint32_t)(t * TMEM_COLS), smem_desc(act[t] + (size_t)(k / 8) * 2048, 2048, 128), bd,
-                       idesc, acc);
+            tc_mma(tmem, a_tmpl | (uint64_t)(a_addr0 + ko), bd, idesc, acc);
+            tc_mma(tmem + (uint32_t)TMEM_COLS, a_tmpl | (uint64_t)(a_addr1 + ko), bd, idesc, acc);
         }
         tc_commit(&mma_bar[b]);
-        consumed = j + 1;
-        // the buffer of chunk j - 1 is free once its MMAs are done: load chunk j - 1 + nbuf into it
-        if (j >= 1 && loaded < total) {
-            const int pb = (int)((j - 1) % nbuf);
+        const int pb = b == 0 ? nbuf - 1 : b - 1;   // the slot of chunk consumed - 1
+        ++consumed;
+        cb = cb + 1 == nbuf ? 0 : cb + 1;
+        cj = cj + 1 == cpt ? 0 : cj + 1;
+        // the buffer of the previous chunk is free once its MMAs are done: load the chunk nbuf ahead into it
+        if (consumed >= 2 && loaded < total) {
             if (!mbar_wait(&mma_bar[pb], (mma_ph >> pb) & 1u)) return false;
             mma_ph ^= 1u << pb;
-            load_chunk(loaded++);
+            load_chunk();
         }
         return true;
     };
 
     if (tid == 0)
-        while (loaded < total && loaded < nbuf) load_chunk(loaded++);
+        while (loaded < total && loaded < nbuf) load_chunk();
     // epilogue roles: warp w reads TMEM lanes 32 (w % 4) .. +31 of tile (w / 4) % 2, column half w / 8
     const int q = warp & 3, t_ep = (warp >> 2) & 1, half = warp >> 3;
     const int row_in_tile = 32 * q + lane;
@@ -555,7 +575,7 @@ fused_mlp_forward_kernel(const __nv_bfloat16 *__restrict__ X, int M, int I, int 
             const int s = tid + k * FTHREADS, t = s >= xsegs ? 1 : 0, s2 = s - t * xsegs;
             const int r = s2 & 127;
             if (s < 2 * xsegs)
-                *reinterpret_cast<uint4 *>(act[t] + (s2 >> 7) * 2048 + (r >> 3) * 128 + (r & 7) * 16) = xr[k];
+                *reinterpret_cast<uint4 *>(act_of(t) + (s2 >> 7) * 2048 + (r >> 3) * 128 + (r & 7) * 16) = xr[k];
         }
     };
     uint32_t layer_ph = 0;
@@ -567,8 +587,8 @@ fused_mlp_forward_kernel(const __nv_bfloat16 *__restrict__ X, int M, int I, int 
         if (xpre && p > 0) {
             x_store();
         } else {
-            fused_stage_x(act[0], X, M, I, G.xkb, (2 * pair) * 128, tid, FTHREADS);
-            fused_stage_x(act[1], X, M, I, G.xkb, (2 * pair + 1) * 128, tid, FTHREADS);
+            fused_stage_x(act_of(0), X, M, I, G.xkb, (2 * pair) * 128, tid, FTHREADS);
+            fused_stage_x(act_of(1), X, M, I, G.xkb, (2 * pair + 1) * 128, tid, FTHREADS);
         }
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         __syncthreads();
@@ -591,7 +611,7 @@ fused_mlp_forward_kernel(const __nv_bfloat16 *__restrict__ X, int M, int I, int 
             const uint32_t taddr = tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(t_ep * TMEM_COLS);
             const float *bias = par + layer * H;
             if (layer < 2) {
-                unsigned char *dst0 = act[t_ep] + (row_in_tile >> 3) * 128 + (row_in_tile & 7) * 16;
+                unsigned char *dst0 = act_of(t_ep) + (row_in_tile >> 3) * 128 + (row_in_tile & 7) * 16;
                 for (int c0 = col_lo; c0 < col_hi; c0 += 32) {
                     const int nb = min(2, (col_hi - c0) / 16);
                     uint32_t v[2][16];
@@ -601,24 +621,23 @@ fused_mlp_forward_kernel(const __nv_bfloat16 *__restrict__ X, int M, int I, int 
                         if (b >= nb) break;
                         const int cb = c0 + 16 * b;
                         const float4 *b4v = reinterpret_cast<const float4 *>(bias + cb);
-                        float x[16];
+                        uint32_t w[8];
 #pragma unroll
                         for (int qq = 0; qq < 4; ++qq) {
                             const float4 bb = b4v[qq];
-                            x[4 * qq] = fmaxf(__uint_as_float(v[b][4 * qq]) + bb.x, 0.f);
-                            x[4 * qq + 1] = fmaxf(__uint_as_float(v[b][4 * qq + 1]) + bb.y, 0.f);
-                            x[4 * qq + 2] = fmaxf(__uint_as_float(v[b][4 * qq + 2]) + bb.z, 0.f);
-                            x[4 * qq + 3] = fmaxf(__uint_as_float(v[b][4 * qq + 3]) + bb.w, 0.f);
+                            w[2 * qq] = relu_bf16x2(__uint_as_float(v[b][4 * qq]) + bb.x,
+                                                    __uint_as_float(v[b][4 * qq + 1]) + bb.y);
+                            w[2 * qq + 1] = relu_bf16x2(__uint_as_float(v[b][4 * qq + 2]) + bb.z,
+                                                        __uint_as_float(v[b][4 * qq + 3]) + bb.w);
                         }
                         unsigned char *dst = dst0 + (size_t)(cb / 8) * 2048;
-                        *reinterpret_cast<uint4 *>(dst) = pack8_bf16(x);
-                        *reinterpret_cast<uint4 *>(dst + 2048) = pack8_bf16(x + 8);
+                        *reinterpret_cast<uint4 *>(dst) = make_uint4(w[0], w[1], w[2], w[3]);
+                        *reinterpret_cast<uint4 *>(dst + 2048) = make_uint4(w[4], w[5], w[6], w[7]);
                     }
                 }
                 asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
             } else {
                 float acc = 0.f;
-                const float *wv = par + 3 * H;
                 for (int c0 = col_lo; c0 < col_hi; c0 += 32) {
                     const int nb = min(2, (col_hi - c0) / 16);
                     uint32_t v[2][16];
@@ -628,17 +647,26 @@ fused_mlp_forward_kernel(const __nv_bfloat16 *__restrict__ X, int M, int I, int 
                         if (b >= nb) break;
                         const int cb = c0 + 16 * b;
 #pragma unroll
-                        for (int e = 0; e < 16; ++e) {
-                            const float h =
-                                __bfloat162float(__float2bfloat16(fmaxf(__uint_as_float(v[b][e]) + bias[cb + e], 0.f)));
-                            acc = fmaf(h, wv[cb + e], acc);
+                        for (int qq = 0; qq < 4; ++qq) {
+                            const float4 bb = reinterpret_cast<const float4 *>(bias + cb)[qq];
+                            const float4 ww = reinterpret_cast<const float4 *>(par + 3 * H + cb)[qq];
+                            const uint32_t h01 = relu_bf16x2(__uint_as_float(v[b][4 * qq]) + bb.x,
+                                                             __uint_as_float(v[b][4 * qq + 1]) + bb.y);
+                            const uint32_t h23 = relu_bf16x2(__uint_as_float(v[b][4 * qq + 2]) + bb.z,
+                                                             __uint_as_float(v[b][4 * qq + 3]) + bb.w);
+                            acc = fmaf(__uint_as_float(h01 << 16), ww.x, acc);
+                            acc = fmaf(__uint_as_float(h01 & 0xFFFF0000u), ww.y, acc);
+                            acc = fmaf(__uint_as_float(h23 << 16), ww.z, acc);
+                            acc = fmaf(__uint_as_float(h23 & 0xFFFF0000u), ww.w, acc);
                         }
                     }
                 }
-                ypart[half][t_ep * 128 + row_in_tile] = acc;
+                // the two column halves' dot products meet in the (now free) activation buffer of tile 0
+                float *ypart = reinterpret_cast<float *>(smem + L.act0);
+                ypart[half * 256 + t_ep * 128 + row_in_tile] = acc;
                 __syncthreads();
                 const int row = (2 * pair + t_ep) * 128 + row_in_tile;
-                if (half == 0 && row < M) y[row] = (acc + ypart[1][t_ep * 128 + row_in_tile]) + par[4 * H];
+                if (half == 0 && row < M) y[row] = (acc + ypart[256 + t_ep * 128 + row_in_tile]) + par[4 * H];
             }
             asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
             __syncthreads();
@@ -791,7 +819,7 @@ int fused_mlp_nbuf(int I, int H)
 {
     if (H % 32 != 0 || H > 256 || I > 256) return 0;
     for (int nb = 4; nb >= 2; --nb)
-        if (mlp::fused_smem(I, H, nb).total <= 220 * 1024) return nb;
+        if (mlp::fused_smem(I, H, nb).total <= 227 * 1024 - 2048) return nb;   // room for the static shared memory
     return 0;
 }
 
