@@ -2182,9 +2182,12 @@ __global__ void __launch_bounds__(SH::NT) features_kernel(const InstMeta *__rest
             f[11] = dn(vn, 1 + bsrc); f[12] = dn(vn, 1 + bdst); f[13] = f[12] - f[11];
             f[14] = c.supply[v] * M.inv_mean_supply;
             f[15] = c.area[v] * M.inv_mean_area;
-            const double ds = (double)c.demq[bsrc], dd = (double)c.demq[bdst];
-            f[16] = (float)(((double)c.base_supq[bsrc] - (same ? 0.0 : (double)c.supq[v]) - ds) / ds);
-            f[17] = (float)(((double)c.base_supq[bdst] + (same ? 0.0 : (double)c.supq[v]) - dd) / dd);
+            // Eq. 2 slack of both BPs after the move, relative to the demand: numerators exact in
+            // fixed point, the ratio in FP32 (FP64 division is slow on this GPU and the features
+            // are rounded to BF16)
+            const long long mv = same ? 0ll : c.supq[v];
+            f[16] = __ll2float_rn(c.base_supq[bsrc] - mv - c.demq[bsrc]) / __ll2float_rn(c.demq[bsrc]);
+            f[17] = __ll2float_rn(c.base_supq[bdst] + mv - c.demq[bdst]) / __ll2float_rn(c.demq[bdst]);
             f[18] = same; f[19] = (gs == gd);
             f[20] = gs < 16 ? (tstar - bs.base_tc[gs]) * inv_t : 0.f;
             f[21] = gd < 16 ? (tstar - bs.base_tc[gd]) * inv_t : 0.f;
@@ -2211,8 +2214,8 @@ __global__ void __launch_bounds__(SH::NT) features_kernel(const InstMeta *__rest
             f[6] = dn(a, f1); f[7] = dn(fl, cc); f[8] = dn(a, cc);
             f[9] = f[5] - f[3] - f[4];
             f[10] = f[6] + f[7] - f[8];
-            f[14] = (float)((double)c.base_supq[b] / (double)c.demq[b]);
-            f[15] = (float)((double)c.barea[b] * c.aq_scale) * M.inv_mean_area / fmaxf(M.mean_fields_per_bp, 1.f);
+            f[14] = __ll2float_rn(c.base_supq[b]) / __ll2float_rn(c.demq[b]);
+            f[15] = __ll2float_rn(c.barea[b]) * c.aq_scale * M.inv_mean_area / fmaxf(M.mean_fields_per_bp, 1.f);
             f[19] = (gs == gd);
             f[20] = gs < 16 ? (tstar - bs.base_tc[gs]) * inv_t : 0.f;
             f[21] = gd < 16 ? (tstar - bs.base_tc[gd]) * inv_t : 0.f;
@@ -2235,8 +2238,9 @@ __global__ void __launch_bounds__(SH::NT) features_kernel(const InstMeta *__rest
             float tcmax = 0.f;
             for (int g = 0; g < c.T; ++g) tcmax = fmaxf(tcmax, bs.base_tc[g]);
             const bool other = (tgs != tgd);
-            const float ad = other && c.tA[tgd] > 0 ? (float)((double)aqm / (double)c.tA[tgd]) : 0.f;
-            const float as = other && c.tA[tgs] > 0 ? (float)((double)aqm / (double)c.tA[tgs]) : 0.f;
+            const float fa = __ll2float_rn(aqm);
+            const float ad = other && c.tA[tgd] > 0 ? fa / __ll2float_rn(c.tA[tgd]) : 0.f;
+            const float as = other && c.tA[tgs] > 0 ? fa / __ll2float_rn(c.tA[tgs]) : 0.f;
             f[34] = fminf(ad, 4.f);
             f[35] = as;
             f[36] = bs.base_tc[tgd] * inv_t * (1.f + f[34]) - 1.f;
