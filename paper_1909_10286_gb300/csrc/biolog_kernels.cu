@@ -2130,7 +2130,24 @@ __global__ void __launch_bounds__(SH::NT) features_kernel(const InstMeta *__rest
     __syncthreads();
     const InstMeta &M = meta[inst];
     Ctx c;
-    if (!stage_instance<SH>(M, bs, smem, sp, prm, use_best, iter, c)) return;
+    // the base plan's per-tour T_compl (and its cost, only when the caller asks for it: the
+    // completion times need the HU assignment alone, the cost the whole score)
+    if (!stage_base<SH>(M, bs, smem, sp, prm, use_best, iter, c)) return;
+    if (tid == 0) {
+        if (base_cost) {
+            score_base<SH>(M, bs, smem, sp, prm, c);
+        } else {
+            c.nbad = bs.nbad;
+            for (int g = 0; g < 16; ++g) bs.base_tc[g] = 0.f;
+            if (bs.nbad == 0) {
+                const MoveRec idm = {4, 0, 0, 0};
+                score_candidate<SH, false, true, 1>(c, prm, idm, __int_as_float(0x7f800000), smem + sp.off_tour, tid,
+                                                    nullptr, nullptr, bs.base_tc, nullptr, nullptr, nullptr, nullptr);
+            }
+        }
+    }
+    __syncthreads();
+    c.nbad = bs.nbad;
     if (blockIdx.x == 0 && tid == 0 && base_cost) *base_cost = bs.base_cost;
     const uint32_t it = bs.iter;   // resolved from the state when the caller passed 0xffffffff
     const float tstar = M.state->tmaxstar;
@@ -2254,11 +2271,17 @@ __global__ void __launch_bounds__(SH::NT) features_kernel(const InstMeta *__rest
         }
 #pragma unroll
         for (int j = 0; j < NFEAT; ++j) f[j] = isfinite(f[j]) ? fminf(fmaxf(f[j], -64.f), 64.f) : 0.f;
-        __nv_bfloat16 *row = feat + (size_t)k * NFEAT;
+        // the row (128 bytes, 16-byte aligned) in eight 16-byte stores
+        uint4 *row = reinterpret_cast<uint4 *>(feat + (size_t)k * NFEAT);
 #pragma unroll
-        for (int j = 0; j < NFEAT; j += 2) {
-            const __nv_bfloat162 pr = __floats2bfloat162_rn(f[j], f[j + 1]);
-            *reinterpret_cast<__nv_bfloat162 *>(row + j) = pr;
+        for (int j = 0; j < NFEAT; j += 8) {
+            uint32_t w[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const __nv_bfloat162 pr = __floats2bfloat162_rn(f[j + 2 * q], f[j + 2 * q + 1]);
+                w[q] = *reinterpret_cast<const uint32_t *>(&pr);
+            }
+            row[j / 8] = make_uint4(w[0], w[1], w[2], w[3]);
         }
     }
 }
