@@ -147,8 +147,13 @@ struct Shape {
 #ifndef BIOLOG_SHAPEA_MINB
 #define BIOLOG_SHAPEA_MINB 2
 #endif
+// Shape B's tour-state columns and survivor records alone fill more than half
+// of an SM's shared memory, so one block resides per SM: no register cap.
+#ifndef BIOLOG_SHAPEB_MINB
+#define BIOLOG_SHAPEB_MINB 1
+#endif
 using ShapeA = Shape<4, 0, true, 256, BIOLOG_SHAPEA_MINB>;   // <= 4 tours, <= 32 HUs/SUs, 32-bit sums
-using ShapeB = Shape<8, 1, true, 128, 4>;                     // <= 8 tours, <= 64 HUs/SUs
+using ShapeB = Shape<8, 1, true, 128, BIOLOG_SHAPEB_MINB>;   // <= 8 tours, <= 64 HUs/SUs
 using ShapeC = Shape<16, 2, false, 128, 2>;                   // <= 16 tours, <= 128 SUs, distances via L2
 
 constexpr int NF32 = 5;   // per-tour floats: LHU, LSU, A, DB2 (2 Dbar), 1/R
@@ -1165,12 +1170,6 @@ __device__ bool stage_instance(const InstMeta &M, BlockShared &bs, unsigned char
     return true;
 }
 
-// Whether the search kernel scores the base plan in warp 0 while the other
-// warps start on the candidates: not in shape B, whose register budget (128 at
-// 4 blocks per SM) does not hold the base scoring next to the candidate loop.
-template <class SH>
-constexpr bool kOverlapBase = SH::MAXT != 8;
-
 // Named barrier 1 (barrier 0 is __syncthreads): the producer warp arrives
 // without waiting, the consumer warps wait until all `n` threads have arrived.
 __device__ __forceinline__ void named_arrive(int n)
@@ -1344,11 +1343,7 @@ __global__ void __launch_bounds__(SH::NT, SH::MINB) search_iteration_kernel(cons
         const InstMeta &M = meta[wi.inst];
         const bool fresh_inst = bs.staged != wi.inst;
         if (fresh_inst) {
-            if constexpr (kOverlapBase<SH>) {
-                if (!stage_base<SH>(M, bs, smem, sp, prm, -1, 0xffffffffu, c)) return;
-            } else {
-                if (!stage_instance<SH>(M, bs, smem, sp, prm, -1, 0xffffffffu, c)) return;
-            }
+            if (!stage_base<SH>(M, bs, smem, sp, prm, -1, 0xffffffffu, c)) return;
             if (tid == 0) bs.staged = wi.inst;
         }
         const float tmax_star = M.state->tmaxstar;
@@ -1381,7 +1376,7 @@ __global__ void __launch_bounds__(SH::NT, SH::MINB) search_iteration_kernel(cons
         // other warps draw and take candidates to the gate; they wait for it (named barrier 1)
         // before their first full score, or at the end if they have none.
         bool memo_wait = false;
-        if (kOverlapBase<SH> && fresh_inst) {
+        if (fresh_inst) {
             if (warp == 0) {
                 if (lane == 0) score_base<SH>(M, bs, smem, sp, prm, c);
                 __syncwarp();
