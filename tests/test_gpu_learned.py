@@ -110,7 +110,7 @@ def _replay_want(S, net, inst_k, k, it, use_best, tmaxstar, pool, n_keep, rf, sa
     for i in range(pool):
         if y[i] <= th:
             keep.append(i)
-        else:
+        elif rf > 0:
             r = O.philox4x32_10([i, salt, 0x5E1EC7 + k, 2], [0x243F6A88, 0x85A308D3])
             if r[0] < cut:
                 keep.append(i)
@@ -146,6 +146,31 @@ def test_learned_step_matches_host_replay():
     new = S.get_state()
     if np.isfinite(c):
         assert o.score(gpu_plan(new, "xold"), gate=0)["cost"] == pytest.approx(c, rel=REL_TOL)
+    net.close()
+    S.close()
+
+
+def test_surrogate_prefilter_step_matches_host_replay():
+    """The surrogate form on the large instance: only the predicted best 1 % of the
+    pool, no random fallback, scored exactly; the list is dealt to about one work
+    item per block."""
+    from paper_1909_10286_gb300.mlp import MLP
+
+    inst = I.make_instance("large", 2)
+    pool, rf = 1 << 17, 0.0
+    n_keep = pool // 100
+    S = biolog.Search([inst], biolog.make_params(n_cand=pool, eps=0.5, seed=1000, gate=1))
+    S.search_step(2)
+    st = S.get_state()
+    it = st["iter"]
+    use_best = int(O.Oracle(inst).eps_select(O.make_params(eps=0.5, seed=1000, gate=1), it))
+    net = MLP(64, 256, max_batch=4096, seed=11, stream=S.stream)   # the fused forward takes any row count
+    want, n_kept = _replay_want(S, net, inst, 0, it, use_best, st["tmaxstar"], pool, n_keep, rf, 0x9E37)
+    assert n_keep // 2 < n_kept < 4 * n_keep
+    S.search_step_learned(net, 1, pool, n_keep, rf)
+    log = S.get_log(it, 1)
+    assert int(log["istar"][0]) == want[1]
+    assert float(log["c_istar"][0]) == float(np.uint32(want[0]).view(np.float32))
     net.close()
     S.close()
 
