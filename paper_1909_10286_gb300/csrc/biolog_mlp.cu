@@ -539,10 +539,22 @@ fused_mlp_forward_kernel(const __nv_bfloat16 *__restrict__ X, int M, int I, int 
         ++consumed;
         cb = cb + 1 == nbuf ? 0 : cb + 1;
         cj = cj + 1 == cpt ? 0 : cj + 1;
-        // the buffer of the previous chunk is free once its MMAs are done: load the chunk nbuf ahead into it
-        if (consumed >= 2 && loaded < total) {
+        // the buffer of the previous chunk is free once its MMAs are done: load the chunk nbuf ahead
+        // into it (unless the end of the previous layer already did, see refill_early)
+        if (consumed >= 2 && loaded < total && loaded == consumed - 2 + nbuf) {
             if (!mbar_wait(&mma_bar[pb], (mma_ph >> pb) & 1u)) return false;
             mma_ph ^= 1u << pb;
+            load_chunk();
+        }
+        return true;
+    };
+    // after a layer's last chunk: once its MMAs are done (the layer is), its buffer takes the chunk
+    // nbuf ahead, so that this copy runs during the epilogue instead of at the next layer's start
+    auto refill_early = [&]() -> bool {
+        if (loaded < total && loaded == consumed - 1 + nbuf) {
+            const int sl = cb == 0 ? nbuf - 1 : cb - 1;   // the buffer of chunk consumed - 1
+            if (!mbar_wait(&mma_bar[sl], (mma_ph >> sl) & 1u)) return false;
+            mma_ph ^= 1u << sl;
             load_chunk();
         }
         return true;
@@ -599,7 +611,8 @@ fused_mlp_forward_kernel(const __nv_bfloat16 *__restrict__ X, int M, int I, int 
                 bool good = true;
                 for (int c = 0; c < nchunks && good; ++c) good = consume_chunk();
                 if (good) tc_commit(&layer_bar);
-                else fail_sh = 1;
+                if (good) good = refill_early();
+                if (!good) fail_sh = 1;
             }
             if (layer == 2 && xpre && p + 1 < my_pairs) x_load(pair + (int)gridDim.x);
             __syncwarp();
