@@ -772,13 +772,22 @@ __global__ void relu_backward_kernel(__nv_bfloat16 *__restrict__ dh, const __nv_
         if (!(__bfloat162float(h[idx]) > 0.f)) dh[idx] = __float2bfloat16(0.f);
 }
 
+// a block covers 32 columns with 32 row lanes: lane r sums rows r, r + 32, ..., then a
+// fixed-order tree over the lanes (deterministic)
 __global__ void colsum_kernel(const __nv_bfloat16 *__restrict__ x, float *__restrict__ out, int M, int H)
 {
-    const int j = blockIdx.x * blockDim.x + threadIdx.x;
-    if (j >= H) return;
+    __shared__ float part[32][33];
+    const int j = blockIdx.x * 32 + threadIdx.x, r = threadIdx.y;
     float s = 0.f;
-    for (int m = 0; m < M; ++m) s += __bfloat162float(x[(size_t)m * H + j]);
-    out[j] = s;
+    if (j < H)
+        for (int m = r; m < M; m += 32) s += __bfloat162float(x[(size_t)m * H + j]);
+    part[r][threadIdx.x] = s;
+    __syncthreads();
+    for (int w = 16; w > 0; w >>= 1) {
+        if (r < w) part[r][threadIdx.x] += part[r + w][threadIdx.x];
+        __syncthreads();
+    }
+    if (r == 0 && j < H) out[j] = part[0][threadIdx.x];
 }
 
 // Adam on FP32 master weights; the BF16 copy used by the GEMMs is refreshed
@@ -893,8 +902,11 @@ cudaError_t launch_head_forward(const void *h, const float *w, const float *b, f
 cudaError_t launch_head_backward(const void *h, const float *w, const float *dy, void *dz, float *dw, float *db, int M,
                                  int H, cudaStream_t s)
 {
-    mlp::head_backward_kernel<<<(H + 127) / 128, 128, 0, s>>>(reinterpret_cast<const __nv_bfloat16 *>(h), w, dy,
-                                                              reinterpret_cast<__nv_bfloat16 *>(dz), dw, db, M, H);
+    // the first (H + 127) / 128 blocks also reduce dW; all of them share the element-wise dz
+    const long long elems = (long long)M * H;
+    const int grid = (int)std::max<long long>((H + 127) / 128, std::min<long long>((elems + 127) / 128, 1024));
+    mlp::head_backward_kernel<<<grid, 128, 0, s>>>(reinterpret_cast<const __nv_bfloat16 *>(h), w, dy,
+                                                   reinterpret_cast<__nv_bfloat16 *>(dz), dw, db, M, H);
     return cudaGetLastError();
 }
 
@@ -907,7 +919,7 @@ cudaError_t launch_relu_backward(void *dh, const void *h, int M, int H, cudaStre
 
 cudaError_t launch_colsum(const void *x, float *out, int M, int H, cudaStream_t s)
 {
-    mlp::colsum_kernel<<<(H + 127) / 128, 128, 0, s>>>(reinterpret_cast<const __nv_bfloat16 *>(x), out, M, H);
+    mlp::colsum_kernel<<<(H + 31) / 32, dim3(32, 32), 0, s>>>(reinterpret_cast<const __nv_bfloat16 *>(x), out, M, H);
     return cudaGetLastError();
 }
 
