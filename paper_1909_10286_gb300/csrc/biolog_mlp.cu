@@ -131,8 +131,13 @@ __device__ __forceinline__ void stage_chunk(__nv_bfloat16 *dst, const __nv_bfloa
 __global__ void __launch_bounds__(THREADS, 1)
 gemm_bf16_tn_kernel(const __nv_bfloat16 *__restrict__ A, const __nv_bfloat16 *__restrict__ B,
                     const float *__restrict__ bias, float *__restrict__ Cf, __nv_bfloat16 *__restrict__ Cb,
-                    int M, int N, int K, int relu, unsigned int *__restrict__ err)
+                    int M, int N, int K, int relu, unsigned int *__restrict__ err, int ksplit)
 {
+    // split K (ksplit > 0, a multiple of BK): grid row y takes K elements [y ksplit, (y + 1) ksplit)
+    // and writes its partial product to slice y of Cf (no bias, ReLU or BF16 output then)
+    const int kbeg = ksplit > 0 ? (int)blockIdx.y * ksplit : 0;
+    const int kend = ksplit > 0 ? min(K, kbeg + ksplit) : K;
+    if (ksplit > 0) Cf += (size_t)blockIdx.y * M * N;
     extern __shared__ __align__(1024) unsigned char smem[];
     __shared__ uint64_t mbar;
     __shared__ uint32_t tmem_base_sh;
@@ -158,7 +163,7 @@ gemm_bf16_tn_kernel(const __nv_bfloat16 *__restrict__ A, const __nv_bfloat16 *__
     const uint32_t idesc = instr_desc(BM, Np);
     uint32_t phase = 0;
     bool ok = true;
-    for (int k0 = 0; k0 < K; k0 += BK) {
+    for (int k0 = kbeg; k0 < kend; k0 += BK) {
         stage_chunk(As, A + (size_t)m0 * K, BM, min(BM, M - m0), K, k0, K);
         stage_chunk(Bs, B, Np, N, K, k0, K);
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");   // generic writes -> tensor-core reads
@@ -169,7 +174,7 @@ gemm_bf16_tn_kernel(const __nv_bfloat16 *__restrict__ A, const __nv_bfloat16 *__
                 if (k0 + s * 16 >= K) break;
                 const uint64_t ad = smem_desc(reinterpret_cast<unsigned char *>(As) + (size_t)s * BM * 32, 128, 256);
                 const uint64_t bd = smem_desc(reinterpret_cast<unsigned char *>(Bs) + (size_t)s * Np * 32, 128, 256);
-                const uint32_t acc = (k0 > 0 || s > 0) ? 1u : 0u;
+                const uint32_t acc = (k0 > kbeg || s > 0) ? 1u : 0u;
                 asm volatile(
                     "{\n\t.reg .pred p;\n\t"
                     "setp.ne.b32 p, %4, 0;\n\t"
@@ -704,6 +709,16 @@ fused_mlp_forward_kernel(const __nv_bfloat16 *__restrict__ X, int M, int I, int 
 }
 
 // ---- elementwise kernels of the MLP ---------------------------------------
+// sum of the split-K partial products, slice by slice in order (deterministic)
+__global__ void splitk_reduce_kernel(const float *__restrict__ part, float *__restrict__ out, int n, int splits)
+{
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        float s = part[i];
+        for (int y = 1; y < splits; ++y) s += part[(size_t)y * n + i];
+        out[i] = s;
+    }
+}
+
 __global__ void transpose_bf16_kernel(const __nv_bfloat16 *__restrict__ in, __nv_bfloat16 *__restrict__ out, int R,
                                       int Cn)
 {
@@ -831,7 +846,26 @@ cudaError_t launch_gemm_bf16(const void *A, const void *B, const float *bias, fl
     const int grid = (M + mlp::BM - 1) / mlp::BM;
     mlp::gemm_bf16_tn_kernel<<<grid, mlp::THREADS, smem, s>>>(
         reinterpret_cast<const __nv_bfloat16 *>(A), reinterpret_cast<const __nv_bfloat16 *>(B), bias, Cf,
-        reinterpret_cast<__nv_bfloat16 *>(Cb), M, N, K, relu, err);
+        reinterpret_cast<__nv_bfloat16 *>(Cb), M, N, K, relu, err, 0);
+    return cudaGetLastError();
+}
+
+// Cf [M x N] FP32 = A B^T over a long K, in up to `splits` slices of K (one grid row each,
+// partial products in `part`, splits x M x N floats), then summed in slice order.
+cudaError_t launch_gemm_bf16_splitk(const void *A, const void *B, float *Cf, float *part, int M, int N, int K,
+                                    int splits, unsigned int *err, cudaStream_t s)
+{
+    const int per = ((K + splits - 1) / splits + mlp::BK - 1) / mlp::BK * mlp::BK;   // K per slice
+    const int ns = (K + per - 1) / per;
+    const size_t smem = mlp_gemm_smem(N);
+    cudaError_t e = cudaFuncSetAttribute(mlp::gemm_bf16_tn_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    mlp::gemm_bf16_tn_kernel<<<dim3((M + mlp::BM - 1) / mlp::BM, ns), mlp::THREADS, smem, s>>>(
+        reinterpret_cast<const __nv_bfloat16 *>(A), reinterpret_cast<const __nv_bfloat16 *>(B), nullptr, part, nullptr,
+        M, N, K, 0, err, per);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    mlp::splitk_reduce_kernel<<<(M * N + 255) / 256, 256, 0, s>>>(part, Cf, M * N, ns);
     return cudaGetLastError();
 }
 

@@ -4,6 +4,7 @@
 #include <cmath>
 #include <cstring>
 #include <random>
+#include <algorithm>
 #include <string>
 #include <vector>
 
@@ -17,6 +18,8 @@ cudaError_t launch_gemm_bf16(const void *A, const void *B, const float *bias, fl
 cudaError_t launch_transpose_bf16(const void *in, void *out, int R, int Cn, cudaStream_t s);
 cudaError_t launch_head_forward(const void *h, const float *w, const float *b, float *y, const float *target, float *dy,
                                 float *loss, int M, int H, cudaStream_t s);
+cudaError_t launch_gemm_bf16_splitk(const void *A, const void *B, float *Cf, float *part, int M, int N, int K,
+                                    int splits, unsigned int *err, cudaStream_t s);
 cudaError_t launch_head_backward(const void *h, const float *w, const float *dy, void *dz, float *dw, float *db, int M,
                                  int H, cudaStream_t s);
 cudaError_t launch_relu_backward(void *dh, const void *h, int M, int H, cudaStream_t s);
@@ -42,6 +45,8 @@ namespace biolog {
 cudaStream_t mlp_stream_of(const bl_mlp *m);
 }
 
+constexpr int kSplitK = 16;   // most K slices of a weight-gradient product
+
 struct bl_mlp {
     int in = 0, H = 0, max_batch = 0;
     cudaStream_t stream = nullptr;
@@ -54,6 +59,7 @@ struct bl_mlp {
     // activations (BF16) and scratch
     uint16_t *h[3] = {}, *dz = nullptr, *dzt = nullptr, *ht = nullptr, *dh = nullptr;
     float *y = nullptr, *dy = nullptr, *loss = nullptr, *gtmp = nullptr;
+    float *kpart = nullptr;   // split-K partial products of the weight gradients (kSplitK x H x max(H, in))
     unsigned int *err = nullptr;
     // inference: BF16 weights of the three layers packed for the fused kernel (repacked
     // after every change of the weights), or none if the shape does not fit it
@@ -164,7 +170,12 @@ int backward(bl_mlp *m, const uint16_t *x, int M)
         // gw[l] [H x K] = dz^T [H x M] * a [M x K]  ->  A = dz^T, B = a^T [K x M]
         MK(m, launch_transpose_bf16(m->dz, m->dzt, M, H, m->stream));
         MK(m, launch_transpose_bf16(a, m->ht, M, K, m->stream));
-        MK(m, launch_gemm_bf16(m->dzt, m->ht, nullptr, m->gw[l], nullptr, H, K, M, 0, m->err, m->stream));
+        // (K of this product is the batch: split it over kSplitK grid rows, so that more than H / 128 blocks work)
+        const int splits = std::min(kSplitK, std::max(1, M / 256));
+        if (splits > 1)
+            MK(m, launch_gemm_bf16_splitk(m->dzt, m->ht, m->gw[l], m->kpart, H, K, M, splits, m->err, m->stream));
+        else
+            MK(m, launch_gemm_bf16(m->dzt, m->ht, nullptr, m->gw[l], nullptr, H, K, M, 0, m->err, m->stream));
         MK(m, launch_colsum(m->dz, m->gb[l], M, H, m->stream));
         if (l > 0) {
             // dh [M x K] = dz [M x H] * W [H x K]  ->  A = dz, B = W^T [K x H]
@@ -236,6 +247,7 @@ int bl_mlp_create(int32_t in_dim, int32_t hidden, int32_t max_batch, uint64_t se
     if (e == cudaSuccess) e = dalloc(m, &m->dzt, wide);
     if (e == cudaSuccess) e = dalloc(m, &m->ht, wide);
     if (e == cudaSuccess) e = dalloc(m, &m->dh, wide);
+    if (e == cudaSuccess) e = dalloc(m, &m->kpart, (size_t)kSplitK * hidden * std::max(hidden, in_dim));
     if (e == cudaSuccess) e = dalloc(m, &m->y, (size_t)max_batch);
     if (e == cudaSuccess) e = dalloc(m, &m->dy, (size_t)max_batch);
     if (e == cudaSuccess) e = dalloc(m, &m->loss, (size_t)1);
