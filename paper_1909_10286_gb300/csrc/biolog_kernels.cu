@@ -2286,42 +2286,79 @@ __global__ void __launch_bounds__(SH::NT) features_kernel(const InstMeta *__rest
 // fraction of the rest as fallback.
 __global__ void select_threshold_kernel(const float *__restrict__ y, int32_t P, int32_t n_keep, float *__restrict__ thresh)
 {
-    __shared__ float sbuf[4096];
+    // The value at rank r of the 4096-prediction sample, found by radix selection on an
+    // order-preserving 32-bit key (8 bits per pass, from the top): the same value a sort of
+    // the sample would put at position r.
+    constexpr int S = 4096;
+    __shared__ unsigned int hist[256];
+    __shared__ unsigned int sel_prefix, sel_rank;
     y += (size_t)blockIdx.x * P;   // block b: instance b of a batch
     thresh += blockIdx.x;
-    const int S = 4096;
-    for (int j = threadIdx.x; j < S; j += blockDim.x) {
+    constexpr int PER = S / 1024;   // keys per thread (blockDim.x = 1024)
+    unsigned int key[PER];
+#pragma unroll
+    for (int q = 0; q < PER; ++q) {
+        const int j = threadIdx.x + q * 1024;
         const long long idx = (long long)j * P / S;
-        const float v = y[idx];
-        sbuf[j] = isfinite(v) ? v : __int_as_float(0x7f800000);
+        float v = y[idx];
+        if (!isfinite(v)) v = __int_as_float(0x7f800000);
+        const unsigned int b = __float_as_uint(v);
+        key[q] = (b & 0x80000000u) ? ~b : (b | 0x80000000u);   // float order -> unsigned order
     }
-    __syncthreads();
-    // bitonic sort of the sample
-    for (int k = 2; k <= S; k <<= 1)
-        for (int jj = k >> 1; jj > 0; jj >>= 1) {
-            for (int t = threadIdx.x; t < S; t += blockDim.x) {
-                const int o = t ^ jj;
-                if (o > t) {
-                    const bool up = ((t & k) == 0);
-                    const float a = sbuf[t], b = sbuf[o];
-                    if ((a > b) == up) { sbuf[t] = b; sbuf[o] = a; }
-                }
-            }
-            __syncthreads();
-        }
     if (threadIdx.x == 0) {
         long long r = (long long)n_keep * S / P;
         if (r >= S) r = S - 1;
         if (r < 0) r = 0;
-        *thresh = sbuf[r];
+        sel_prefix = 0u;
+        sel_rank = (unsigned int)r;
+    }
+    unsigned int mask = 0u;
+    for (int shift = 24; shift >= 0; shift -= 8) {
+        if (threadIdx.x < 256) hist[threadIdx.x] = 0u;
+        __syncthreads();
+        const unsigned int prefix = sel_prefix;
+#pragma unroll
+        for (int q = 0; q < PER; ++q)
+            if ((key[q] & mask) == prefix) atomicAdd(&hist[(key[q] >> shift) & 255u], 1u);
+        __syncthreads();
+        if (threadIdx.x < 32) {
+            // lane l owns digits 8l .. 8l + 7: find the digit whose cumulative count passes the rank
+            const int lane = threadIdx.x;
+            unsigned int c[8], tot = 0u;
+#pragma unroll
+            for (int d = 0; d < 8; ++d) { c[d] = hist[8 * lane + d]; tot += c[d]; }
+            unsigned int incl = tot;
+            for (int o = 1; o < 32; o <<= 1) {
+                const unsigned int t = __shfl_up_sync(0xffffffffu, incl, o);
+                if (lane >= o) incl += t;
+            }
+            const unsigned int excl = incl - tot, r = sel_rank;
+            if (r >= excl && r < incl) {   // exactly one lane
+                unsigned int below = excl;
+                int d = 0;
+                while (below + c[d] <= r) { below += c[d]; ++d; }
+                sel_prefix = prefix | ((unsigned int)(8 * lane + d) << shift);
+                sel_rank = r - below;
+            }
+        }
+        mask |= 255u << shift;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        const unsigned int k = sel_prefix;
+        *thresh = __uint_as_float((k & 0x80000000u) ? (k & 0x7fffffffu) : ~k);
     }
 }
 
-__global__ void select_compact_kernel(const float *__restrict__ y, int32_t P, const float *__restrict__ thresh,
-                                      float rand_frac, uint32_t salt, uint32_t *__restrict__ list,
-                                      int32_t *__restrict__ count)
+__global__ void __launch_bounds__(256) select_compact_kernel(const float *__restrict__ y, int32_t P,
+                                                            const float *__restrict__ thresh, float rand_frac,
+                                                            uint32_t salt, uint32_t *__restrict__ list,
+                                                            int32_t *__restrict__ count)
 {
-    // grid row b: instance b of a batch (its own predictions, threshold, list and count)
+    // grid row b: instance b of a batch (its own predictions, threshold, list and count).
+    // Each warp gathers its kept indices in shared memory and appends them with one atomic
+    // per 224+ entries (the list's order is free: the argmin over it is order-independent).
+    __shared__ uint32_t wbuf[8][256];
     const uint32_t b = blockIdx.y;
     y += (size_t)b * P;
     list += (size_t)b * P;
@@ -2329,22 +2366,36 @@ __global__ void select_compact_kernel(const float *__restrict__ y, int32_t P, co
     count += b;
     const float th = *thresh;
     const uint32_t cut = (uint32_t)(rand_frac * 4294967295.0f);
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < P; i += gridDim.x * blockDim.x) {
-        bool keep = y[i] <= th;
-        if (!keep) {
-            uint32_t r[4] = {(uint32_t)i, salt, 0x5E1EC7u + b, 2u};
-            philox10(r, 0x243F6A88u, 0x85A308D3u);
-            keep = r[0] < cut;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint32_t *buf = wbuf[warp];
+    int n = 0;   // warp-uniform: entries in buf
+    auto flush = [&]() {
+        int off = 0;
+        if (lane == 0) off = atomicAdd(count, n);
+        off = __shfl_sync(0xffffffffu, off, 0);
+        for (int k = lane; k < n; k += 32) list[off + k] = buf[k];
+        __syncwarp();
+        n = 0;
+    };
+    const int stride = gridDim.x * blockDim.x;
+    for (int base = blockIdx.x * blockDim.x + warp * 32; base < P; base += stride) {
+        const int i = base + lane;
+        bool keep = false;
+        if (i < P) {
+            keep = y[i] <= th;
+            if (!keep) {
+                uint32_t r[4] = {(uint32_t)i, salt, 0x5E1EC7u + b, 2u};
+                philox10(r, 0x243F6A88u, 0x85A308D3u);
+                keep = r[0] < cut;
+            }
         }
-        const unsigned act = __activemask();
-        const unsigned ball = __ballot_sync(act, keep);
-        const int lane = threadIdx.x & 31;
-        const int leader = __ffs(act) - 1;
-        int base = 0;
-        if (lane == leader && ball) base = atomicAdd(count, __popc(ball));
-        base = __shfl_sync(act, base, leader);
-        if (keep) list[base + __popc(ball & ((1u << lane) - 1u))] = (uint32_t)i;
+        const unsigned ball = __ballot_sync(0xffffffffu, keep);
+        if (keep) buf[n + __popc(ball & ((1u << lane) - 1u))] = (uint32_t)i;
+        n += __popc(ball);
+        __syncwarp();
+        if (n > 256 - 32) flush();
     }
+    if (n > 0) flush();
 }
 
 // ---------------------------------------------------------------------------
