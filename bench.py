@@ -215,6 +215,30 @@ def _peaks():
         return {}
 
 
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "dram_traffic.txt")
+
+
+def _traffic(line_name: str):
+    """DRAM bytes per launch of a line's dominant kernel, from one ncu capture listed in
+    profiles/dram_traffic.txt, or None if there is none or the kernel's source file has
+    changed since (its SHA-256 is recorded beside the figure)."""
+    import hashlib
+
+    try:
+        rows = [r.split() for r in open(TRAFFIC_FILE) if r.strip() and not r.startswith("#")]
+    except OSError:
+        return None
+    for r in rows:
+        if len(r) >= 4 and r[0] == line_name:
+            src, want_sha, nbytes = r[1], r[2], r[3]
+            try:
+                sha = hashlib.sha256(open(os.path.join(ROOT, src), "rb").read()).hexdigest()
+            except OSError:
+                return None
+            return int(nbytes) if sha == want_sha else None
+    return None
+
+
 def oracle_throughput(inst, params_kw, n_cand, budget_s, threads, max_iters=50, state=None):
     """The CPU oracle's Algorithm 1 on the host cores: iterations of m candidates
     (m <= n_cand, chosen so the run takes about budget_s). Returns (cand/s, m, iters, threads)."""
@@ -377,7 +401,8 @@ def run_learned(args, ws, rank, local):
             "gpu_launches": args.steps * 5, "clocks": clk,
             "e2e": {"value": None, "note": "the end-to-end number is on the default paper line"},
             "roofline": {"bound": "tensor", "kernel": "fused_mlp_forward_kernel", "achieved": achieved, "peak": peak,
-                         "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None, "ms_per_launch": ms_mlp,
+                         "unit": "TFLOP/s", "frac": achieved / peak, "traffic": _traffic(args.workload),
+                         "ms_per_launch": ms_mlp,
                          "flop_per_launch": flop,
                          "peak_basis": "bf16_tflops (burst) of MEASURED_PEAKS.json; kernel timed alone"}}
     net.close()
@@ -568,7 +593,7 @@ def main():
         peak = sms * 4 * 32 * f_mhz * 1e6 / 1e12            # lane-ops/s: 4 schedulers x 32 lanes per SM
         achieved = w_per * n_total / (ms_step / 1e3) / 1e12
         line["roofline"] = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tlane-op/s",
-                            "frac": achieved / peak, "traffic": None, "ops_per_candidate": w_per,
+                            "frac": achieved / peak, "traffic": _traffic(args.workload), "ops_per_candidate": w_per,
                             "peak_basis": f"{sms} SMs x 4 schedulers x 32 lanes x {f_mhz:.0f} MHz (sm_max_mhz of "
                                           "MEASURED_PEAKS.json)"}
         if len(insts) > 1:
