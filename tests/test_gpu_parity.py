@@ -124,6 +124,13 @@ def test_search_near_the_shared_memory_limit(F, T, n, iters):
     assert n_ties <= 1
 
 
+def test_search_at_the_largest_shape():
+    """16 tours, 64 HUs and 128 SUs: the most the largest kernel shape holds (SU sets of two
+    64-bit words); 300 fields and 20 BPs."""
+    _, _, n_ties = _trajectory(I.make_sized(300, 20, 16, 64, 128, seed=16), 2048, 3)
+    assert n_ties <= 1
+
+
 def test_checkpoint_resume_is_exact():
     inst = I.make_instance("paper", 8)
     A, _, _ = pair(inst, 4096)
