@@ -70,7 +70,7 @@ def tune(instances, n_cand: int, base_params: dict | None = None, iters: int = 8
     import torch
 
     gpu = torch.cuda.get_device_name()
-    key = f"v2|{gpu}|{_bucket(instances, n_cand)}"   # v2: lanes per candidate searched too
+    key = f"v3|{gpu}|{_bucket(instances, n_cand)}"   # v3: the six-tour shape reads distances through L2
     with _lock:
         cache = _load() if use_cache else {}
         if key in cache:

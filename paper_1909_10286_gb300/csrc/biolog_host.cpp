@@ -418,10 +418,8 @@ int pick_shape(const std::vector<HostInst> &insts)
         for (long long v : h.sufq.m) b += v;
         fits32 = fits32 && a < (1ll << 31) && b < (1ll << 31);
     }
-    if (maxS <= 64 && maxH <= 64 && maxTotal <= kSmemDistLimit) {
-        if (maxT <= 4 && maxS <= 32 && maxH <= 32 && fits32) return SHAPE_T4_S64_DSMEM;
-        if (maxT <= 8) return SHAPE_T8_S64_DSMEM;
-    }
+    if (maxT <= 4 && maxS <= 32 && maxH <= 32 && fits32 && maxTotal <= kSmemDistLimit) return SHAPE_T4_S64_DSMEM;
+    if (maxT <= 6 && maxS <= 64 && maxH <= 64) return SHAPE_T6_S64_GMEM;
     return SHAPE_T16_S128_GMEM;
 }
 
@@ -563,8 +561,8 @@ int init_common(const bl_instance *insts, int32_t n_inst, const bl_params *param
         h->cfg.max_B = std::max(h->cfg.max_B, hi.B);
         h->cfg.max_T = std::max(h->cfg.max_T, hi.T);
     }
-    // shared memory of a shape for these instances; a shape that stages the distances
-    // but does not fit gives way to the one that reads them through L2
+    // shared memory of a shape for these instances; shape A, which stages the distances,
+    // gives way to a shape that reads them through L2 when it does not fit
     auto smem_of = [&](int sh, int32_t &prefix) {
         prefix = 0;
         for (const HostInst &hi : h->insts)
@@ -575,8 +573,8 @@ int init_common(const bl_instance *insts, int32_t n_inst, const bl_params *param
     const size_t smem_limit = 227 * 1024 - 2048;   // leave room for the static shared memory of the kernels
     int32_t prefix = 0;
     size_t smem = smem_of(shape, prefix);
-    if (smem > smem_limit && shape != SHAPE_T16_S128_GMEM) {
-        shape = SHAPE_T16_S128_GMEM;
+    if (smem > smem_limit && shape == SHAPE_T4_S64_DSMEM) {
+        shape = SHAPE_T6_S64_GMEM;   // shape A's limits are within shape B's
         smem = smem_of(shape, prefix);
     }
     h->cfg.shape = shape;

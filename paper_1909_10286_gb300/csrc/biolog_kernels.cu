@@ -147,13 +147,10 @@ struct Shape {
 #ifndef BIOLOG_SHAPEA_MINB
 #define BIOLOG_SHAPEA_MINB 2
 #endif
-// Shape B's tour-state columns and survivor records alone fill more than half
-// of an SM's shared memory, so one block resides per SM: no register cap.
-#ifndef BIOLOG_SHAPEB_MINB
-#define BIOLOG_SHAPEB_MINB 1
-#endif
+// Shape B reads the distances through L2: its tour-state columns and survivor
+// records for 6 tours then take about 100 KB, and two blocks reside per SM.
 using ShapeA = Shape<4, 0, true, 256, BIOLOG_SHAPEA_MINB>;   // <= 4 tours, <= 32 HUs/SUs, 32-bit sums
-using ShapeB = Shape<8, 1, true, 128, BIOLOG_SHAPEB_MINB>;   // <= 8 tours, <= 64 HUs/SUs
+using ShapeB = Shape<6, 1, false, 128, 2>;                   // <= 6 tours, <= 64 HUs/SUs, distances via L2
 using ShapeC = Shape<16, 2, false, 128, 2>;                   // <= 16 tours, <= 128 SUs, distances via L2
 
 constexpr int NF32 = 5;   // per-tour floats: LHU, LSU, A, DB2 (2 Dbar), 1/R
@@ -530,7 +527,7 @@ struct Survivor {
     unsigned amask;
     float tmax;
 };
-// kept for shapes of at most 8 tours, where the records fit in shared memory next to the rest
+// kept for shapes of at most 8 tours (A and B), where the records fit in shared memory next to the rest
 template <class SH>
 constexpr bool kKeepSurvivors = SH::MAXT <= 8;
 
@@ -2530,20 +2527,20 @@ __global__ void __launch_bounds__(SH::NT) argmin_noalloc_kernel(const InstMeta *
 // ---------------------------------------------------------------------------
 // Host-side launch wrappers
 // ---------------------------------------------------------------------------
-int max_tours_of(int32_t shape) { return shape == SHAPE_T4_S64_DSMEM ? 4 : shape == SHAPE_T8_S64_DSMEM ? 8 : 16; }
+int max_tours_of(int32_t shape) { return shape == SHAPE_T4_S64_DSMEM ? 4 : shape == SHAPE_T6_S64_GMEM ? 6 : 16; }
 int threads_of(int32_t shape)
 {
-    return shape == SHAPE_T4_S64_DSMEM ? ShapeA::NT : shape == SHAPE_T8_S64_DSMEM ? ShapeB::NT : ShapeC::NT;
+    return shape == SHAPE_T4_S64_DSMEM ? ShapeA::NT : shape == SHAPE_T6_S64_GMEM ? ShapeB::NT : ShapeC::NT;
 }
 int max_su_of(int32_t shape) { return shape == SHAPE_T16_S128_GMEM ? 128 : (shape == SHAPE_T4_S64_DSMEM ? 32 : 64); }
-bool dist_in_smem(int32_t shape) { return shape != SHAPE_T16_S128_GMEM; }
+bool dist_in_smem(int32_t shape) { return shape == SHAPE_T4_S64_DSMEM; }
 
 static SmemPlan plan_for(const LaunchCfg &cfg)
 {
     switch (cfg.shape) {
     case SHAPE_T4_S64_DSMEM:
         return carve_shape<ShapeA>(cfg.max_prefix, cfg.max_plan_len, cfg.max_F, cfg.max_B, cfg.max_T);
-    case SHAPE_T8_S64_DSMEM:
+    case SHAPE_T6_S64_GMEM:
         return carve_shape<ShapeB>(cfg.max_prefix, cfg.max_plan_len, cfg.max_F, cfg.max_B, cfg.max_T);
     default:
         return carve_shape<ShapeC>(cfg.max_prefix, cfg.max_plan_len, cfg.max_F, cfg.max_B, cfg.max_T);
@@ -2568,7 +2565,7 @@ static cudaError_t with_coop_kernel(int32_t shape, int32_t lanes, F &&f)
         if (lanes == 4) return f(search_iteration_coop_kernel<ShapeA, 4>);
         if (lanes == 8) return f(search_iteration_coop_kernel<ShapeA, 8>);
         break;
-    case SHAPE_T8_S64_DSMEM:
+    case SHAPE_T6_S64_GMEM:
         if (lanes == 8) return f(search_iteration_coop_kernel<ShapeB, 8>);
         if (lanes == 16) return f(search_iteration_coop_kernel<ShapeB, 16>);
         break;
@@ -2583,7 +2580,7 @@ bool coop_supported(int32_t shape, int32_t lanes)
 {
     switch (shape) {
     case SHAPE_T4_S64_DSMEM: return lanes == 4 || lanes == 8;
-    case SHAPE_T8_S64_DSMEM: return lanes == 8 || lanes == 16;
+    case SHAPE_T6_S64_GMEM: return lanes == 8 || lanes == 16;
     default: return lanes == 16 || lanes == 32;
     }
 }
@@ -2628,7 +2625,7 @@ cudaError_t configure_kernels(int32_t shape, size_t smem)
 {
     switch (shape) {
     case SHAPE_T4_S64_DSMEM: return set_attrs<ShapeA>(smem);
-    case SHAPE_T8_S64_DSMEM: return set_attrs<ShapeB>(smem);
+    case SHAPE_T6_S64_GMEM: return set_attrs<ShapeB>(smem);
     default: return set_attrs<ShapeC>(smem);
     }
 }
@@ -2643,7 +2640,7 @@ int search_blocks_per_sm(int32_t shape, size_t smem)
     case SHAPE_T4_S64_DSMEM:
         e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, search_iteration_kernel<ShapeA>, ShapeA::NT, smem);
         break;
-    case SHAPE_T8_S64_DSMEM:
+    case SHAPE_T6_S64_GMEM:
         e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, search_iteration_kernel<ShapeB>, ShapeB::NT, smem);
         break;
     default:
@@ -2673,7 +2670,7 @@ cudaError_t launch_search_iteration(const LaunchCfg &cfg, const InstMeta *d_meta
         search_iteration_kernel<ShapeA><<<cfg.grid, ShapeA::NT, sp.total, s>>>(
             d_meta, d_work, n_work, prm, sp, slot_key, slot_tmax, slot_base, cand_list, cand_count, list_stride);
         break;
-    case SHAPE_T8_S64_DSMEM:
+    case SHAPE_T6_S64_GMEM:
         search_iteration_kernel<ShapeB><<<cfg.grid, ShapeB::NT, sp.total, s>>>(
             d_meta, d_work, n_work, prm, sp, slot_key, slot_tmax, slot_base, cand_list, cand_count, list_stride);
         break;
@@ -2730,7 +2727,7 @@ cudaError_t launch_argmin_noalloc(const LaunchCfg &cfg, const InstMeta *d_meta, 
         e = cudaFuncSetAttribute(argmin_noalloc_kernel<ShapeA>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sp.total);
         if (e == cudaSuccess) argmin_noalloc_kernel<ShapeA><<<grid, nt, sp.total, s>>>(NA_ARGS);
         break;
-    case SHAPE_T8_S64_DSMEM:
+    case SHAPE_T6_S64_GMEM:
         e = cudaFuncSetAttribute(argmin_noalloc_kernel<ShapeB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sp.total);
         if (e == cudaSuccess) argmin_noalloc_kernel<ShapeB><<<grid, nt, sp.total, s>>>(NA_ARGS);
         break;
@@ -2763,7 +2760,7 @@ cudaError_t launch_features(const LaunchCfg &cfg, const InstMeta *d_meta, int32_
         if (e == cudaSuccess)
             features_kernel<ShapeA><<<dim3(grid, gy), nt, sp.total, s>>>(d_meta, inst, use_best, iter, i0, n, prm, sp, f, d_base_cost, batched);
         break;
-    case SHAPE_T8_S64_DSMEM:
+    case SHAPE_T6_S64_GMEM:
         e = cudaFuncSetAttribute(features_kernel<ShapeB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sp.total);
         if (e == cudaSuccess)
             features_kernel<ShapeB><<<dim3(grid, gy), nt, sp.total, s>>>(d_meta, inst, use_best, iter, i0, n, prm, sp, f, d_base_cost, batched);
@@ -2803,7 +2800,7 @@ cudaError_t launch_score_dump(const LaunchCfg &cfg, const InstMeta *d_meta, int3
                   d_nsu, d_tcompl, d_twait, d_tcost, d_hu_tour, d_su_tour
     switch (cfg.shape) {
     case SHAPE_T4_S64_DSMEM: score_dump_kernel<ShapeA><<<grid, nt, sp.total, s>>>(DUMP_ARGS); break;
-    case SHAPE_T8_S64_DSMEM: score_dump_kernel<ShapeB><<<grid, nt, sp.total, s>>>(DUMP_ARGS); break;
+    case SHAPE_T6_S64_GMEM: score_dump_kernel<ShapeB><<<grid, nt, sp.total, s>>>(DUMP_ARGS); break;
     default: score_dump_kernel<ShapeC><<<grid, nt, sp.total, s>>>(DUMP_ARGS);
     }
 #undef DUMP_ARGS
@@ -2823,7 +2820,7 @@ cudaError_t launch_decode(const LaunchCfg &cfg, const InstMeta *d_meta, int32_t 
     case SHAPE_T4_S64_DSMEM:
         decode_kernel<ShapeA><<<grid, nt, sp.total, s>>>(d_meta, inst, use_best, iter, d_idx, n, prm, sp, d_plans);
         break;
-    case SHAPE_T8_S64_DSMEM:
+    case SHAPE_T6_S64_GMEM:
         decode_kernel<ShapeB><<<grid, nt, sp.total, s>>>(d_meta, inst, use_best, iter, d_idx, n, prm, sp, d_plans);
         break;
     default:

@@ -45,7 +45,7 @@ def test_workspace_query_and_validation_without_gpu(lib):
     with pytest.raises(biolog.BiologError) as e:
         biolog.workspace_bytes([infeas], p)
     assert e.value.code == biolog.BL_EINFEASIBLE_INSTANCE
-    # tables that fit in shared memory only without the kernel's other buffers: accepted
+    # instances whose distance tables do not fit in shared memory next to the kernel's buffers: accepted
     for F, T in ((180, 5), (186, 8)):
         assert biolog.workspace_bytes([I.make_sized(F, 5, T, 10, 20, seed=F)], p) > 0
     big = I.make_instance("large", 0)
