@@ -98,7 +98,7 @@ typedef struct bl_params {
     int32_t lanes_per_cand;  /* 0 or 1: one thread scores a candidate; 4, 8, 16 or 32: a group
                                 of that many lanes of a warp scores it together, lane g holding
                                 tour g (>= the largest tour count; 4 or 8 for <= 4 tours, 8 or
-                                16 for <= 8, 16 or 32 above; else BL_EINVAL). Same results. */
+                                16 for <= 6, 16 or 32 above; else BL_EINVAL). Same results. */
     void *workspace;         /* device, optional: caller-owned buffer of
                                 bl_workspace_bytes() bytes, 256-byte aligned; NULL = the
                                 library allocates and frees its own */
