@@ -420,6 +420,7 @@ int pick_shape(const std::vector<HostInst> &insts)
     }
     if (maxT <= 4 && maxS <= 32 && maxH <= 32 && fits32 && maxTotal <= kSmemDistLimit) return SHAPE_T4_S64_DSMEM;
     if (maxT <= 6 && maxS <= 64 && maxH <= 64) return SHAPE_T6_S64_GMEM;
+    if (maxT <= 10) return SHAPE_T10_S128_GMEM;
     return SHAPE_T16_S128_GMEM;
 }
 
@@ -589,7 +590,7 @@ int init_common(const bl_instance *insts, int32_t n_inst, const bl_params *param
         return BL_EINVAL;
     }
     for (const HostInst &hi : h->insts)
-        if (hi.T > max_tours_of(shape) || hi.S > max_su_of(shape) || hi.H > (shape == SHAPE_T16_S128_GMEM ? 64 : max_su_of(shape))) {
+        if (hi.T > max_tours_of(shape) || hi.S > max_su_of(shape) || hi.H > ((shape == SHAPE_T16_S128_GMEM || shape == SHAPE_T10_S128_GMEM) ? 64 : max_su_of(shape))) {
             g_error = "no kernel shape fits";
             delete h;
             return BL_ETOO_LARGE;

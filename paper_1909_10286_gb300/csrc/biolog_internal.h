@@ -101,6 +101,7 @@ enum ShapeClass : int32_t {
     SHAPE_T4_S64_DSMEM = 0,   // tours <= 4,  HUs and SUs <= 32 (32-bit sets and sums), distances in shared memory
     SHAPE_T6_S64_GMEM = 1,    // tours <= 6,  HUs and SUs <= 64, distances read through L2
     SHAPE_T16_S128_GMEM = 2,  // tours <= 16, SUs <= 128, distances read through L2
+    SHAPE_T10_S128_GMEM = 3,  // tours <= 10, SUs <= 128, distances read through L2
 };
 
 struct LaunchCfg {

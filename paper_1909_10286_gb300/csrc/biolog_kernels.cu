@@ -152,6 +152,7 @@ struct Shape {
 using ShapeA = Shape<4, 0, true, 256, BIOLOG_SHAPEA_MINB>;   // <= 4 tours, <= 32 HUs/SUs, 32-bit sums
 using ShapeB = Shape<6, 1, false, 128, 2>;                   // <= 6 tours, <= 64 HUs/SUs, distances via L2
 using ShapeC = Shape<16, 2, false, 128, 2>;                   // <= 16 tours, <= 128 SUs, distances via L2
+using ShapeD = Shape<10, 2, false, 128, 2>;                   // <= 10 tours, <= 128 SUs, distances via L2
 
 constexpr int NF32 = 5;   // per-tour floats: LHU, LSU, A, DB2 (2 Dbar), 1/R
 constexpr int WQ = 64;    // per-warp queue of feasible candidates (ring buffer)
@@ -2527,12 +2528,20 @@ __global__ void __launch_bounds__(SH::NT) argmin_noalloc_kernel(const InstMeta *
 // ---------------------------------------------------------------------------
 // Host-side launch wrappers
 // ---------------------------------------------------------------------------
-int max_tours_of(int32_t shape) { return shape == SHAPE_T4_S64_DSMEM ? 4 : shape == SHAPE_T6_S64_GMEM ? 6 : 16; }
+int max_tours_of(int32_t shape)
+{
+    return shape == SHAPE_T4_S64_DSMEM ? 4 : shape == SHAPE_T6_S64_GMEM ? 6 : shape == SHAPE_T10_S128_GMEM ? 10 : 16;
+}
 int threads_of(int32_t shape)
 {
-    return shape == SHAPE_T4_S64_DSMEM ? ShapeA::NT : shape == SHAPE_T6_S64_GMEM ? ShapeB::NT : ShapeC::NT;
+    return shape == SHAPE_T4_S64_DSMEM ? ShapeA::NT
+           : shape == SHAPE_T6_S64_GMEM ? ShapeB::NT
+           : shape == SHAPE_T10_S128_GMEM ? ShapeD::NT : ShapeC::NT;
 }
-int max_su_of(int32_t shape) { return shape == SHAPE_T16_S128_GMEM ? 128 : (shape == SHAPE_T4_S64_DSMEM ? 32 : 64); }
+int max_su_of(int32_t shape)
+{
+    return (shape == SHAPE_T16_S128_GMEM || shape == SHAPE_T10_S128_GMEM) ? 128 : (shape == SHAPE_T4_S64_DSMEM ? 32 : 64);
+}
 bool dist_in_smem(int32_t shape) { return shape == SHAPE_T4_S64_DSMEM; }
 
 static SmemPlan plan_for(const LaunchCfg &cfg)
@@ -2542,6 +2551,8 @@ static SmemPlan plan_for(const LaunchCfg &cfg)
         return carve_shape<ShapeA>(cfg.max_prefix, cfg.max_plan_len, cfg.max_F, cfg.max_B, cfg.max_T);
     case SHAPE_T6_S64_GMEM:
         return carve_shape<ShapeB>(cfg.max_prefix, cfg.max_plan_len, cfg.max_F, cfg.max_B, cfg.max_T);
+    case SHAPE_T10_S128_GMEM:
+        return carve_shape<ShapeD>(cfg.max_prefix, cfg.max_plan_len, cfg.max_F, cfg.max_B, cfg.max_T);
     default:
         return carve_shape<ShapeC>(cfg.max_prefix, cfg.max_plan_len, cfg.max_F, cfg.max_B, cfg.max_T);
     }
@@ -2568,6 +2579,10 @@ static cudaError_t with_coop_kernel(int32_t shape, int32_t lanes, F &&f)
     case SHAPE_T6_S64_GMEM:
         if (lanes == 8) return f(search_iteration_coop_kernel<ShapeB, 8>);
         if (lanes == 16) return f(search_iteration_coop_kernel<ShapeB, 16>);
+        break;
+    case SHAPE_T10_S128_GMEM:
+        if (lanes == 16) return f(search_iteration_coop_kernel<ShapeD, 16>);
+        if (lanes == 32) return f(search_iteration_coop_kernel<ShapeD, 32>);
         break;
     default:
         if (lanes == 16) return f(search_iteration_coop_kernel<ShapeC, 16>);
@@ -2626,6 +2641,8 @@ cudaError_t configure_kernels(int32_t shape, size_t smem)
     switch (shape) {
     case SHAPE_T4_S64_DSMEM: return set_attrs<ShapeA>(smem);
     case SHAPE_T6_S64_GMEM: return set_attrs<ShapeB>(smem);
+    case SHAPE_T10_S128_GMEM:
+        return set_attrs<ShapeD>(smem);
     default: return set_attrs<ShapeC>(smem);
     }
 }
@@ -2642,6 +2659,9 @@ int search_blocks_per_sm(int32_t shape, size_t smem)
         break;
     case SHAPE_T6_S64_GMEM:
         e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, search_iteration_kernel<ShapeB>, ShapeB::NT, smem);
+        break;
+    case SHAPE_T10_S128_GMEM:
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, search_iteration_kernel<ShapeD>, ShapeD::NT, smem);
         break;
     default:
         e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, search_iteration_kernel<ShapeC>, ShapeC::NT, smem);
@@ -2672,6 +2692,10 @@ cudaError_t launch_search_iteration(const LaunchCfg &cfg, const InstMeta *d_meta
         break;
     case SHAPE_T6_S64_GMEM:
         search_iteration_kernel<ShapeB><<<cfg.grid, ShapeB::NT, sp.total, s>>>(
+            d_meta, d_work, n_work, prm, sp, slot_key, slot_tmax, slot_base, cand_list, cand_count, list_stride);
+        break;
+    case SHAPE_T10_S128_GMEM:
+        search_iteration_kernel<ShapeD><<<cfg.grid, ShapeD::NT, sp.total, s>>>(
             d_meta, d_work, n_work, prm, sp, slot_key, slot_tmax, slot_base, cand_list, cand_count, list_stride);
         break;
     default:
@@ -2731,6 +2755,10 @@ cudaError_t launch_argmin_noalloc(const LaunchCfg &cfg, const InstMeta *d_meta, 
         e = cudaFuncSetAttribute(argmin_noalloc_kernel<ShapeB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sp.total);
         if (e == cudaSuccess) argmin_noalloc_kernel<ShapeB><<<grid, nt, sp.total, s>>>(NA_ARGS);
         break;
+    case SHAPE_T10_S128_GMEM:
+        e = cudaFuncSetAttribute(argmin_noalloc_kernel<ShapeD>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sp.total);
+        if (e == cudaSuccess) argmin_noalloc_kernel<ShapeD><<<grid, nt, sp.total, s>>>(NA_ARGS);
+        break;
     default:
         e = cudaFuncSetAttribute(argmin_noalloc_kernel<ShapeC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sp.total);
         if (e == cudaSuccess) argmin_noalloc_kernel<ShapeC><<<grid, nt, sp.total, s>>>(NA_ARGS);
@@ -2764,6 +2792,11 @@ cudaError_t launch_features(const LaunchCfg &cfg, const InstMeta *d_meta, int32_
         e = cudaFuncSetAttribute(features_kernel<ShapeB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sp.total);
         if (e == cudaSuccess)
             features_kernel<ShapeB><<<dim3(grid, gy), nt, sp.total, s>>>(d_meta, inst, use_best, iter, i0, n, prm, sp, f, d_base_cost, batched);
+        break;
+    case SHAPE_T10_S128_GMEM:
+        e = cudaFuncSetAttribute(features_kernel<ShapeD>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sp.total);
+        if (e == cudaSuccess)
+            features_kernel<ShapeD><<<dim3(grid, gy), nt, sp.total, s>>>(d_meta, inst, use_best, iter, i0, n, prm, sp, f, d_base_cost, batched);
         break;
     default:
         e = cudaFuncSetAttribute(features_kernel<ShapeC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sp.total);
@@ -2801,6 +2834,9 @@ cudaError_t launch_score_dump(const LaunchCfg &cfg, const InstMeta *d_meta, int3
     switch (cfg.shape) {
     case SHAPE_T4_S64_DSMEM: score_dump_kernel<ShapeA><<<grid, nt, sp.total, s>>>(DUMP_ARGS); break;
     case SHAPE_T6_S64_GMEM: score_dump_kernel<ShapeB><<<grid, nt, sp.total, s>>>(DUMP_ARGS); break;
+    case SHAPE_T10_S128_GMEM:
+        score_dump_kernel<ShapeD><<<grid, nt, sp.total, s>>>(DUMP_ARGS);
+        break;
     default: score_dump_kernel<ShapeC><<<grid, nt, sp.total, s>>>(DUMP_ARGS);
     }
 #undef DUMP_ARGS
@@ -2822,6 +2858,9 @@ cudaError_t launch_decode(const LaunchCfg &cfg, const InstMeta *d_meta, int32_t 
         break;
     case SHAPE_T6_S64_GMEM:
         decode_kernel<ShapeB><<<grid, nt, sp.total, s>>>(d_meta, inst, use_best, iter, d_idx, n, prm, sp, d_plans);
+        break;
+    case SHAPE_T10_S128_GMEM:
+        decode_kernel<ShapeD><<<grid, nt, sp.total, s>>>(d_meta, inst, use_best, iter, d_idx, n, prm, sp, d_plans);
         break;
     default:
         decode_kernel<ShapeC><<<grid, nt, sp.total, s>>>(d_meta, inst, use_best, iter, d_idx, n, prm, sp, d_plans);
