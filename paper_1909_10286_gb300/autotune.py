@@ -70,7 +70,7 @@ def tune(instances, n_cand: int, base_params: dict | None = None, iters: int = 8
     import torch
 
     gpu = torch.cuda.get_device_name()
-    key = f"v3|{gpu}|{_bucket(instances, n_cand)}"   # v3: the six-tour shape reads distances through L2
+    key = f"v4|{gpu}|{_bucket(instances, n_cand)}"   # v4: six- and ten-tour shapes, two blocks per SM
     with _lock:
         cache = _load() if use_cache else {}
         if key in cache:
