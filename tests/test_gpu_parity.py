@@ -117,7 +117,7 @@ def test_search_trajectory_matches_oracle(wl, seed, n, iters, kw):
 @pytest.mark.parametrize("F,T,n,iters", [(140, 5, 3000, 6), (180, 5, 3000, 6), (186, 8, 2048, 4)])
 def test_search_near_the_shared_memory_limit(F, T, n, iters):
     """Instances of 140 to 186 fields with 5 and 8 tours: the six-tour shape (distances
-    through L2, first-stage records in shared memory) and, for 8 tours, the sixteen-tour
+    through L2, first-stage records in shared memory) and, for 8 tours, the ten-tour
     shape. Either way the search follows the oracle."""
     _, _, n_ties = _trajectory(I.make_sized(F, 5, T, 10, 20, seed=F), n, iters)
     assert n_ties <= 1
