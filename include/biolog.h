@@ -211,13 +211,17 @@ int bl_decode_candidates(bl_handle *h, int32_t inst, int32_t use_best, uint32_t 
    Nothing is allocated: the kernel's scratch (one partial result per block,
    at most 1024 blocks, and a completion counter; 16,640 bytes) is a static
    array in the library's device code that every GPU loading the library
-   holds until the process exits. The first call on a device looks up that
-   array's device address (with the device current), so make the first call
-   before any stream capture. All calls on a device share the array: the
-   counter is cleared before each launch, and calls that overlap on the GPU
-   (e.g. on two streams) race and must not be issued. Errors: BL_EINVAL,
-   BL_ETOO_LARGE when n < 1, n > BL_NOALLOC_MAX_CAND or i0 + n overflows,
-   BL_ECUDA. */
+   holds until the process exits. The current device must be the one the
+   handle was created on (BL_EINVAL otherwise). The first call on a handle
+   looks up that array's device address, so make it before any stream
+   capture. All calls on a device share the array: the counter is cleared
+   before each launch, and calls that overlap on the GPU (e.g. on two
+   streams) race and must not be issued. If a block's bounded staging wait
+   gives up, the outputs are still written but hold no result (*d_key =
+   ~0, *d_tmax = NaN) and the handle's next synchronising call reports
+   BL_ETIMEOUT. Errors: BL_ETOO_LARGE when n < 1, n > BL_NOALLOC_MAX_CAND,
+   i0 < 0 or i0 + n > INT32_MAX (checked first, for any handle, NULL
+   included), then BL_EINVAL, BL_ESTATE, BL_ECUDA. */
 #define BL_NOALLOC_MAX_CAND (1 << 28)
 int bl_argmin_noalloc(bl_handle *h, int32_t inst, int32_t use_best, uint32_t iter, float tmax_star, int32_t i0,
                       int32_t n, uint64_t *d_key, float *d_tmax);

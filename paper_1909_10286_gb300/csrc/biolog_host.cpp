@@ -352,6 +352,8 @@ struct bl_handle {
     float *l_y = nullptr, *l_thresh = nullptr;
     uint32_t *l_list = nullptr;
     int32_t *l_count = nullptr;
+    int dev = -1;                      // the device current at plan_init
+    void *noalloc_scratch = nullptr;   // device address of bl_argmin_noalloc's static scratch (first call)
     std::string err;
     bool failed = false;
     template <class T>
@@ -606,6 +608,7 @@ int init_common(const bl_instance *insts, int32_t n_inst, const bl_params *param
     if (!size_only) {
         int dev = 0;
         CK(nullptr, cudaGetDevice(&dev));
+        h->dev = dev;
         CK(nullptr, cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
         cudaError_t e = configure_kernels(shape, h->cfg.smem);
         if (e != cudaSuccess) { delete h; return cuda_fail(nullptr, e, "configure_kernels"); }
@@ -961,14 +964,23 @@ int bl_decode_candidates(bl_handle *h, int32_t inst, int32_t use_best, uint32_t 
 int bl_argmin_noalloc(bl_handle *h, int32_t inst, int32_t use_best, uint32_t iter, float tmax_star, int32_t i0,
                       int32_t n, uint64_t *d_key, float *d_tmax)
 {
-    if (!h || inst < 0 || inst >= h->n_inst || i0 < 0 || !d_key || !d_tmax) return BL_EINVAL;
-    if (h->failed) return BL_ESTATE;
-    if (n < 1 || n > BL_NOALLOC_MAX_CAND || (int64_t)i0 + (int64_t)n > (int64_t)INT32_MAX) {
-        h->err = "bl_argmin_noalloc: n must be in [1, BL_NOALLOC_MAX_CAND] and i0 + n must fit in int32";
+    // the size limits come first: they do not depend on the handle
+    if (n < 1 || n > BL_NOALLOC_MAX_CAND || i0 < 0 || (int64_t)i0 + (int64_t)n > (int64_t)INT32_MAX) {
+        const char *msg = "bl_argmin_noalloc: n must be in [1, BL_NOALLOC_MAX_CAND], i0 >= 0 and i0 + n <= INT32_MAX";
+        if (h) h->err = msg; else g_error = msg;
         return BL_ETOO_LARGE;
     }
+    if (!h || inst < 0 || inst >= h->n_inst || !d_key || !d_tmax) return BL_EINVAL;
+    if (h->failed) return BL_ESTATE;
+    int dev = -1;
+    CK(h, cudaGetDevice(&dev));
+    if (dev != h->dev) {
+        h->err = "bl_argmin_noalloc: the current device is not the handle's device";
+        return BL_EINVAL;
+    }
+    if (!h->noalloc_scratch) CK(h, noalloc_scratch_address(&h->noalloc_scratch));
     CK(h, launch_argmin_noalloc(h->cfg, h->at<InstMeta>(h->ws.meta), inst, use_best, iter, tmax_star, i0, n, h->sp,
-                                reinterpret_cast<unsigned long long *>(d_key), d_tmax, h->stream));
+                                h->noalloc_scratch, reinterpret_cast<unsigned long long *>(d_key), d_tmax, h->stream));
     return BL_OK;
 }
 

@@ -135,9 +135,10 @@ cudaError_t launch_score_dump(const LaunchCfg &cfg, const InstMeta *d_meta, int3
 cudaError_t launch_decode(const LaunchCfg &cfg, const InstMeta *d_meta, int32_t inst, int32_t use_best,
                           uint32_t iter, const int32_t *d_idx, int32_t n, SearchParams prm, int16_t *d_plans,
                           cudaStream_t s);
+cudaError_t noalloc_scratch_address(void **ptr);
 cudaError_t launch_argmin_noalloc(const LaunchCfg &cfg, const InstMeta *d_meta, int32_t inst, int32_t use_best,
                                   uint32_t iter, float tmax_star, int32_t i0, int32_t n, SearchParams prm,
-                                  unsigned long long *d_key, float *d_tmax, cudaStream_t s);
+                                  void *scratch, unsigned long long *d_key, float *d_tmax, cudaStream_t s);
 size_t shared_bytes(int32_t shape, int32_t threads, int32_t max_prefix, int32_t max_plan_len, int32_t max_F,
                     int32_t max_B, int32_t max_T);
 cudaError_t configure_kernels(int32_t shape, size_t smem);

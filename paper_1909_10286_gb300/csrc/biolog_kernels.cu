@@ -26,7 +26,6 @@
 // shared memory, one column per thread (more tours).
 #include <cstdint>
 #include <cuda_bf16.h>
-#include <mutex>
 #include <type_traits>
 #include <cuda_runtime.h>
 
@@ -2432,21 +2431,26 @@ __global__ void __launch_bounds__(SH::NT) argmin_noalloc_kernel(const InstMeta *
     __syncthreads();
     const InstMeta &M = meta[inst];
     Ctx c;
-    if (!stage_instance<SH>(M, bs, smem, sp, prm, use_best, iter, c)) return;
+    // A block whose staging wait gave up (error flag set) scores nothing but still
+    // reports an empty partial result, so the last block always writes the outputs:
+    // after a timeout *out_key is ~0 (no candidate) and *out_tmax NaN.
+    const bool staged = stage_instance<SH>(M, bs, smem, sp, prm, use_best, iter, c);
     unsigned char *tstate = smem + sp.off_tour;
     int32_t *qidx = (int32_t *)(smem + sp.off_qidx) + warp * WQ;
     int2 *qmv = (int2 *)(smem + sp.off_qmv) + warp * WQ;
     unsigned long long best = ~0ull;
-    float best_t = 0.f;
+    float best_t = staged ? 0.f : __int_as_float(0x7fc00000);
     int qhead = 0, qcount = 0;
-    const int stride = NT * gridDim.x;
-    const int c1 = i0 + n;
-    for (int base = i0 + blockIdx.x * NT + warp * 32; base < c1 || qcount > 0; base += stride) {
+    // 64-bit positions: i0 + n may lie within one grid stride of INT32_MAX
+    const long long stride = (long long)NT * gridDim.x;
+    const long long c1 = staged ? (long long)i0 + n : (long long)i0;
+    for (long long base = (long long)i0 + (long long)blockIdx.x * NT + warp * 32; base < c1 || qcount > 0;
+         base += stride) {
         if (base < c1) {
-            const int i = base + lane;
+            const int i = (int)(base + lane);   // < c1 <= INT32_MAX when i < c1
             bool feas = false;
             MoveRec m = {4, 0, 0, 0};
-            if (i < c1) {
+            if (base + lane < c1) {
                 m = draw_move(c, prm, (uint32_t)i, bs.iter, M.inst_idx);
                 feas = demand_ok(c, m);
                 if (!feas) {
@@ -2705,36 +2709,20 @@ cudaError_t launch_search_iteration(const LaunchCfg &cfg, const InstMeta *d_meta
     return cudaGetLastError();
 }
 
-// Device address of the no-allocation scratch array, looked up once per device
-// with that device current (the name is only a host-side stand-in: passing it to
-// a kernel would hand the GPU a host address).
-static void *g_noalloc_ptr[64];
-static std::mutex g_noalloc_mutex;
-
-static cudaError_t noalloc_scratch(void **ptr)
+// Device address of the no-allocation scratch array on the current device (the
+// name is only a host-side stand-in: passing it to a kernel would hand the GPU a
+// host address). The caller looks it up once per handle, with the handle's
+// device current, and keeps it: a handle does not outlive its device's context.
+cudaError_t noalloc_scratch_address(void **ptr)
 {
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e != cudaSuccess) return e;
-    if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
-    std::lock_guard<std::mutex> lock(g_noalloc_mutex);
-    if (!g_noalloc_ptr[dev]) {
-        void *p = nullptr;
-        e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-        if (e != cudaSuccess) return e;
-        g_noalloc_ptr[dev] = p;
-    }
-    *ptr = g_noalloc_ptr[dev];
-    return cudaSuccess;
+    return cudaGetSymbolAddress(ptr, g_noalloc_scratch);
 }
 
 cudaError_t launch_argmin_noalloc(const LaunchCfg &cfg, const InstMeta *d_meta, int32_t inst, int32_t use_best,
                                   uint32_t iter, float tmax_star, int32_t i0, int32_t n, SearchParams prm,
-                                  unsigned long long *d_key, float *d_tmax, cudaStream_t s)
+                                  void *scratch, unsigned long long *d_key, float *d_tmax, cudaStream_t s)
 {
-    void *scratch = nullptr;
-    cudaError_t e = noalloc_scratch(&scratch);
-    if (e != cudaSuccess) return e;
+    cudaError_t e = cudaSuccess;
     // the counter must start at zero; the partial results are written before they are read
     e = cudaMemsetAsync(scratch, 0, 256, s);
     if (e != cudaSuccess) return e;

@@ -65,3 +65,23 @@ def test_no_cpu_fallback():
         pytest.skip("a GPU is present")
     with pytest.raises(biolog.BiologError):
         biolog.plan_init(I.make_instance("tiny", 0), biolog.make_params(n_cand=64))
+
+
+def test_argmin_noalloc_size_checks_without_gpu(lib):
+    """bl_argmin_noalloc checks n and i0 + n before it looks at the handle, so the
+    limits are testable with a NULL handle and no GPU: positions up to INT32_MAX
+    are legal, one past it is not."""
+    import ctypes as C
+
+    def call(i0, n):
+        return lib.bl_argmin_noalloc(None, 0, 0, 0, C.c_float(0.0), int(i0), int(n), C.c_void_p(8), C.c_void_p(8))
+
+    int32_max = 2**31 - 1
+    max_cand = 1 << 28
+    for i0, n in ((0, 0), (0, -1), (0, max_cand + 1), (-1, 10), (int32_max - 9, 11), (int32_max, 1),
+                  (int32_max - max_cand + 1, max_cand)):
+        assert call(i0, n) == biolog.BL_ETOO_LARGE, (i0, n)
+        assert b"INT32_MAX" in lib.bl_global_error()
+    # legal sizes reach the handle check (NULL handle -> BL_EINVAL), the last ones end at INT32_MAX
+    for i0, n in ((0, 1), (0, max_cand), (int32_max - 10, 10), (int32_max - 1, 1), (int32_max - max_cand, max_cand)):
+        assert call(i0, n) == biolog.BL_EINVAL, (i0, n)
