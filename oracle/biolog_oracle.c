@@ -23,7 +23,8 @@
  * picks, acceptance and termination tests, the gate) records its relative gap
  * |a-b|/scale; the minimum over one candidate is its margin. Exact equality is
  * a structural tie (both sides resolve it with the same tie rule) and does not
- * lower the margin.
+ * lower the margin. or_score_plan_trace returns every counted gap with its
+ * decision site, so tests can check each one against a hand derivation.
  */
 #include <math.h>
 #include <stdint.h>
@@ -501,14 +502,42 @@ static int64_t ceil_ratio(double a, double b)
     return k;
 }
 
-/* relative decision gap; exact equality is a structural tie */
-static void note_gap(double *margin, double a, double b, double scale)
+/* Decision sites, for the trace of the gaps a score counts (the margin pins):
+   the three picks of a local-minimisation round (Algorithm 2, Step 2), its
+   acceptance test (Step 4), its termination test (Step 5), for the HU step
+   and the SU step, and the completion-time gate (Sec. 2.5). */
+enum {
+    GAP_HU_MAX = 1, GAP_HU_MAX2 = 2, GAP_HU_MIN = 3, GAP_HU_ACCEPT = 4, GAP_HU_STOP = 5,
+    GAP_SU_MAX = 6, GAP_SU_MAX2 = 7, GAP_SU_MIN = 8, GAP_SU_ACCEPT = 9, GAP_SU_STOP = 10,
+    GAP_GATE = 11
+};
+
+typedef struct {
+    int32_t site;
+    int32_t pad;
+    double a, b, scale;   /* the compared values and the scale of their relative gap */
+} or_gap;
+
+/* optional trace of the calling thread (single-plan scoring only) */
+static __thread or_gap *g_trace;
+static __thread int g_trace_n, g_trace_cap;
+
+/* relative decision gap |a - b| / scale; exact equality is a structural tie
+   and is neither counted nor traced */
+static void note_gap(int site, double *margin, double a, double b, double scale)
 {
     if (a == b || !isfinite(a) || !isfinite(b)) return;
     double s = scale;
     if (!(s > 0.0)) s = fmax(fabs(a), fabs(b));
     double m = fabs(a - b) / s;
     if (m < *margin) *margin = m;
+    if (g_trace) {
+        if (g_trace_n < g_trace_cap) {
+            or_gap *r = &g_trace[g_trace_n];
+            r->site = site; r->pad = 0; r->a = a; r->b = b; r->scale = s;
+        }
+        ++g_trace_n;
+    }
 }
 
 /* ------------------------------------------------------------------------ */
@@ -527,7 +556,7 @@ typedef struct {
     double LHU[64], LSU[64], A[64], Dbar[64];
 } route_agg;
 
-static void pick_max_max2_min(const double *val, const double *scale, const int *act, int na,
+static void pick_max_max2_min(int site0, const double *val, const double *scale, const int *act, int na,
                               int *gmax, int *gmax2, int *gmin, double *margin, double *ops)
 {
     /* Algorithm 2, Step 2: g_max = argmax, g_max,2nd = argmax over the rest,
@@ -543,9 +572,10 @@ static void pick_max_max2_min(const double *val, const double *scale, const int 
     /* margins of the three picks: the winner against every competitor */
     for (int j = 0; j < na; ++j) {
         int g = act[j];
-        if (g != a) note_gap(margin, val[a], val[g], fmax(scale[a], scale[g]));
-        if (g != a && g != a2) note_gap(margin, val[a2], val[g], fmax(scale[a2], scale[g]));
-        if (na > 2 && g != a && g != a2 && g != m) note_gap(margin, val[m], val[g], fmax(scale[m], scale[g]));
+        if (g != a) note_gap(site0, margin, val[a], val[g], fmax(scale[a], scale[g]));
+        if (g != a && g != a2) note_gap(site0 + 1, margin, val[a2], val[g], fmax(scale[a2], scale[g]));
+        if (na > 2 && g != a && g != a2 && g != m)
+            note_gap(site0 + 2, margin, val[m], val[g], fmax(scale[m], scale[g]));
     }
     *gmax = a; *gmax2 = a2; *gmin = m;
 }
@@ -589,7 +619,7 @@ static void hu_assign(const or_ctx *c, const or_params *prm, const route_agg *ra
     for (int round = 0; round < c->H; ++round) {
         if (na < 2) break;
         int gmax, gmax2, gmin;
-        pick_max_max2_min(Tc, scale, act, na, &gmax, &gmax2, &gmin, margin, ops);
+        pick_max_max2_min(GAP_HU_MAX, Tc, scale, act, na, &gmax, &gmax2, &gmin, margin, ops);
         int cnt = 0, last = -1;
         for (int k = 0; k < c->H; ++k) if (hu_tour[c->hu_sorted[k]] == gmin) { ++cnt; last = k; }
         if (cnt <= 1) break;
@@ -605,7 +635,7 @@ static void hu_assign(const or_ctx *c, const or_params *prm, const route_agg *ra
             double ref = (na == 2) ? tmn : Tc[gmax2];
             *ops += 8;
             int is_last = (k == last);
-            if (!is_last) note_gap(margin, tmx, ref, fmax(tmx, ref));
+            if (!is_last) note_gap(GAP_HU_ACCEPT, margin, tmx, ref, fmax(tmx, ref));
             if (tmx < ref || is_last) {
                 moved = h; newTmax = tmx; newTmin = tmn; newRmax = rmax; newRmin = rmin;
                 break;
@@ -617,7 +647,7 @@ static void hu_assign(const or_ctx *c, const or_params *prm, const route_agg *ra
         scale[gmax] = newTmax; scale[gmin] = newTmin;
         double nm = -INFINITY;
         for (int j = 0; j < na; ++j) { if (Tc[act[j]] > nm) nm = Tc[act[j]]; *ops += 1; }
-        note_gap(margin, nm, old_max, fmax(nm, old_max));
+        note_gap(GAP_HU_STOP, margin, nm, old_max, fmax(nm, old_max));
         if (!(nm < old_max)) {
             hu_tour[moved] = gmin;
             Tc[gmax] = saveTmax; Tc[gmin] = saveTmin; R[gmax] = saveRmax; R[gmin] = saveRmin;
@@ -663,7 +693,7 @@ static void su_assign(const or_ctx *c, const or_params *prm, const route_agg *ra
     for (int round = 0; round < c->S; ++round) {
         if (na < 2) break;
         int gmax, gmax2, gmin;
-        pick_max_max2_min(Tw, scale, act, na, &gmax, &gmax2, &gmin, margin, ops);
+        pick_max_max2_min(GAP_SU_MAX, Tw, scale, act, na, &gmax, &gmax2, &gmin, margin, ops);
         int cnt = 0, last = -1;
         for (int k = 0; k < c->S; ++k) if (su_tour[c->su_sorted[k]] == gmin) { ++cnt; last = k; }
         if (cnt <= 1) break;
@@ -681,7 +711,7 @@ static void su_assign(const or_ctx *c, const or_params *prm, const route_agg *ra
             double ref_scale = (na == 2) ? sc_mn : scale[gmax2];
             *ops += 12;
             int is_last = (k == last);
-            if (!is_last) note_gap(margin, tmx, ref, fmax(sc_mx, ref_scale));
+            if (!is_last) note_gap(GAP_SU_ACCEPT, margin, tmx, ref, fmax(sc_mx, ref_scale));
             if (tmx < ref || is_last) { moved = s; nmx = tmx; nmn = tmn; smx = sc_mx; smn = sc_mn; break; }
             su_tour[s] = gmin;
         }
@@ -689,7 +719,7 @@ static void su_assign(const or_ctx *c, const or_params *prm, const route_agg *ra
         Tw[gmax] = nmx; Tw[gmin] = nmn; scale[gmax] = smx; scale[gmin] = smn;
         double nm = -INFINITY, nm_scale = 0.0;
         for (int j = 0; j < na; ++j) { int g = act[j]; if (Tw[g] > nm) { nm = Tw[g]; nm_scale = scale[g]; } *ops += 1; }
-        note_gap(margin, nm, old_max, fmax(nm_scale, sscmx));
+        note_gap(GAP_SU_STOP, margin, nm, old_max, fmax(nm_scale, sscmx));
         if (!(nm < old_max)) {
             su_tour[moved] = gmin;
             Tw[gmax] = svmx; Tw[gmin] = svmn; scale[gmax] = sscmx; scale[gmin] = sscmn;
@@ -836,7 +866,7 @@ static void score_plan(const or_ctx *c, const or_params *prm, const oplan *p, do
        literal "does not decrease" (>=). */
     res->tmax = tmax;
     if (gate) {
-        note_gap(&margin, tmax, tmax_star, fmax(tmax, tmax_star));
+        note_gap(GAP_GATE, &margin, tmax, tmax_star, fmax(tmax, tmax_star));
         ops += 1;
         if ((gate == 1 && tmax > tmax_star) || (gate == 2 && tmax >= tmax_star)) {
             cost = INFINITY;
@@ -898,6 +928,24 @@ int or_score_plan(const or_ctx *c, const or_params *prm, const int16_t *bp_order
     score_plan(c, prm, &p, tmax_star, gate, res, &det);
     plan_release(&p);
     return 0;
+}
+
+/* or_score_plan with the trace of every decision gap the score counts, in the
+   order taken (at most cap records; returns their number, or -1 for a bad
+   plan). The margin is the smallest |a - b| / scale of the trace. */
+int or_score_plan_trace(const or_ctx *c, const or_params *prm, const int16_t *bp_order, const int16_t *tour_cnt,
+                        const int16_t *field_order, const int16_t *bp_cnt, double tmax_star, int32_t gate,
+                        or_score *res, or_gap *trace, int32_t cap)
+{
+    oplan p;
+    plan_alloc(&p, c->T, c->B, c->F);
+    if (plan_from_enc(&p, bp_order, tour_cnt, field_order, bp_cnt)) { plan_release(&p); return -1; }
+    g_trace = trace; g_trace_n = 0; g_trace_cap = cap;
+    score_plan(c, prm, &p, tmax_star, gate, res, NULL);
+    const int n = g_trace_n;
+    g_trace = NULL; g_trace_n = 0; g_trace_cap = 0;
+    plan_release(&p);
+    return n;
 }
 
 /* Trace of the cost's edges for one plan (Fig. 1): kind 0 = HU drive,

@@ -59,6 +59,16 @@ class _Score(C.Structure):
                 ("ops", C.c_double)]
 
 
+class _Gap(C.Structure):
+    _fields_ = [("site", C.c_int32), ("pad", C.c_int32), ("a", C.c_double), ("b", C.c_double),
+                ("scale", C.c_double)]
+
+
+# decision sites of the gap trace (the C file's GAP_* numbering)
+GAP_SITES = {1: "hu_max", 2: "hu_max2", 3: "hu_min", 4: "hu_accept", 5: "hu_stop",
+             6: "su_max", 7: "su_max2", 8: "su_min", 9: "su_accept", 10: "su_stop", 11: "gate"}
+
+
 class _State(C.Structure):
     _fields_ = [("xold_bp_order", C.c_void_p), ("xold_tour_cnt", C.c_void_p), ("xold_field_order", C.c_void_p),
                 ("xold_bp_cnt", C.c_void_p), ("xbest_bp_order", C.c_void_p), ("xbest_tour_cnt", C.c_void_p),
@@ -83,6 +93,8 @@ def lib():
             L.or_apply.argtypes = [C.c_void_p, i16p, i16p, i16p, i16p, i16p, i16p, i16p, i16p, i16p]
             L.or_score_plan.argtypes = [C.c_void_p, C.POINTER(Params), i16p, i16p, i16p, i16p, C.c_double, C.c_int32,
                                         C.POINTER(_Score), i32p, i32p, f64p, f64p, f64p, i32p, i32p]
+            L.or_score_plan_trace.argtypes = [C.c_void_p, C.POINTER(Params), i16p, i16p, i16p, i16p, C.c_double,
+                                              C.c_int32, C.POINTER(_Score), C.c_void_p, C.c_int32]
             L.or_trace_edges.argtypes = [C.c_void_p, i16p, i16p, i16p, i16p, i32p, i32p, i32p, i32p, C.c_int32]
             L.or_eps_select.argtypes = [C.POINTER(Params), C.c_uint32]
             L.or_validate_enc.argtypes = [C.c_int, C.c_int, C.c_int, i16p, i16p, i16p, i16p]
@@ -211,6 +223,21 @@ class Oracle:
             raise ValueError("bad plan")
         return dict(feasible=bool(r.feasible), cost=r.cost, tmax=r.tmax, margin=r.margin, ops=r.ops,
                     n_hu=n_hu, n_su=n_su, tcompl=tc, twait=tw, tcost=tcost, hu_tour=hu, su_tour=su)
+
+    def decision_trace(self, plan: Plan, params: Params | None = None, tmax_star=np.inf, gate=0, cap=4096):
+        """Every decision gap the score of `plan` counts, in order: (site, a, b, scale), where the
+        site names the decision (GAP_SITES) and |a - b| / scale is its relative gap; plus the score."""
+        params = params or make_params()
+        buf = (_Gap * cap)()
+        r = _Score()
+        n = lib().or_score_plan_trace(self._h, C.byref(params), *plan.arrays(), float(tmax_star), int(gate),
+                                      C.byref(r), C.cast(buf, C.c_void_p), int(cap))
+        if n < 0:
+            raise ValueError("bad plan")
+        if n > cap:
+            raise ValueError("trace longer than cap")
+        rows = [(GAP_SITES[buf[k].site], buf[k].a, buf[k].b, buf[k].scale) for k in range(n)]
+        return rows, dict(feasible=bool(r.feasible), cost=r.cost, tmax=r.tmax, margin=r.margin)
 
     def trace_edges(self, plan: Plan):
         cap = 8 * (self.F + self.B + self.T) + 16

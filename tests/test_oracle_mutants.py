@@ -36,6 +36,22 @@ MUTANTS = {
     "hu_round_robin_reversed": ("for (int k = 0; k < c->H; ++k) hu_tour[c->hu_sorted[k]] = act[k % na];",
                                 "for (int k = 0; k < c->H; ++k) hu_tour[c->hu_sorted[k]] = act[na - 1 - k % na];"),
     "wait_fill_sign": ("return drive - fill;", "return drive + fill;"),
+    # decision margins (the gaps that decide which candidates escape the strict FP32-FP64 comparison)
+    "margin_pick_smaller_scale": ("if (g != a) note_gap(site0, margin, val[a], val[g], fmax(scale[a], scale[g]));",
+                                  "if (g != a) note_gap(site0, margin, val[a], val[g], fmin(scale[a], scale[g]));"),
+    "margin_min_pick_wrong_operand": ("note_gap(site0 + 2, margin, val[m], val[g], fmax(scale[m], scale[g]));",
+                                      "note_gap(site0 + 2, margin, val[a2], val[g], fmax(scale[a2], scale[g]));"),
+    "margin_hu_accept_dropped": ("if (!is_last) note_gap(GAP_HU_ACCEPT, margin, tmx, ref, fmax(tmx, ref));",
+                                 "(void)is_last;"),
+    "margin_su_accept_counts_last": ("if (!is_last) note_gap(GAP_SU_ACCEPT,", "note_gap(GAP_SU_ACCEPT,"),
+    "margin_su_accept_wrong_scale": ("fmax(sc_mx, ref_scale)", "fmax(sc_mn, ref_scale)"),
+    "margin_hu_stop_wrong_operand": ("note_gap(GAP_HU_STOP, margin, nm, old_max, fmax(nm, old_max));",
+                                     "note_gap(GAP_HU_STOP, margin, nm, Tc[gmax2], fmax(nm, Tc[gmax2]));"),
+    "margin_su_stop_new_scale": ("fmax(nm_scale, sscmx)", "nm_scale"),
+    "margin_gate_dropped": ("note_gap(GAP_GATE, &margin, tmax, tmax_star, fmax(tmax, tmax_star));", "(void)0;"),
+    "margin_keeps_largest": ("if (m < *margin) *margin = m;", "if (m > *margin || isinf(*margin)) *margin = m;"),
+    "margin_su_scale_max_of_terms": ("if (scale) *scale = fabs(drive) + fabs(fill);",
+                                     "if (scale) *scale = fmax(fabs(drive), fabs(fill));"),
 }
 
 

@@ -188,6 +188,96 @@ def test_hu_local_min_hand_trace(oracle_mod):
     assert list(f["hu_tour"]) == [0, 1, 2, 0, 1, 2, 0, 1, 2]
 
 
+def _gaps(rows):
+    return [abs(a - b) / sc for _, a, b, sc in rows]
+
+
+def _check_trace(got, want, rel=1e-12):
+    """The traced decision gaps equal the hand-derived ones (site, a, b, scale), as multisets."""
+    key = lambda r: (r[0], round(r[1], 9), round(r[2], 9))  # noqa: E731
+    g, w = sorted(got, key=key), sorted(want, key=key)
+    assert [r[0] for r in g] == [r[0] for r in w], (g, w)
+    for (sg, ag, bg, cg), (sw, aw, bw, cw) in zip(g, w):
+        assert (ag, bg, cg) == pytest.approx((aw, bw, cw), rel=rel), (sg, (ag, bg, cg), (aw, bw, cw))
+
+
+def test_hu_decision_margins_hand_trace(oracle_mod):
+    """The decision gaps of the HU trace above (Algorithm 2's Steps 2, 4 and 5 applied to HUs),
+    derived by hand from the same rounds. A pick's gap compares the picked tour's T with each
+    competitor's, scaled by the larger of their T; an acceptance test compares T(g_max) after the
+    trial move with T(g_max2), scaled by the larger; the last member of g_min is accepted without a
+    test; the termination test compares the new maximum with the old one, scaled by the larger.
+      R1: T = [2, 3, 11]; max t2 vs t0, t1; max2 t1 vs t0; no min competitor with 3 tours;
+          trials 1, 4 (not 7, the last); stop: 8.2 vs 11.
+      R2: T = [3.4, 3, 8.2]; max t2 vs t0, t1; max2 t0 vs t1; trials 2, 5; stop: 1+180/33 vs 8.2.
+      R3: T = [3.4, 1+30/7, 1+180/33]; max t2 vs t0, t1; max2 t1 vs t0; trial 1; stop: 13 vs 1+180/33.
+    The margin is the smallest gap: 0.4/3.4 (R2, max2)."""
+    o = oracle_mod.Oracle(_hu_trace_instance())
+    rows, sc = o.decision_trace(oracle_mod.Plan.from_lists([[0], [1], [2]], [[0], [1], [2]]))
+    t1 = 1 + 30 / 7
+    t2 = 1 + 180 / 33
+    want = [
+        ("hu_max", 11, 2, 11), ("hu_max", 11, 3, 11), ("hu_max2", 3, 2, 3),
+        ("hu_accept", 1 + 180 / 19, 3, 1 + 180 / 19), ("hu_accept", 1 + 180 / 22, 3, 1 + 180 / 22),
+        ("hu_stop", 8.2, 11, 11),
+        ("hu_max", 8.2, 3.4, 8.2), ("hu_max", 8.2, 3, 8.2), ("hu_max2", 3.4, 3, 3.4),
+        ("hu_accept", 1 + 180 / 27, 3.4, 1 + 180 / 27), ("hu_accept", 7, 3.4, 7),
+        ("hu_stop", t2, 8.2, 8.2),
+        ("hu_max", t2, 3.4, t2), ("hu_max", t2, t1, t2), ("hu_max2", t1, 3.4, t1),
+        ("hu_accept", 1 + 180 / 34, t1, 1 + 180 / 34),
+        ("hu_stop", 13, t2, 13),
+    ]
+    _check_trace(rows, want)
+    assert sc["margin"] == pytest.approx(0.4 / 3.4, rel=1e-12)
+    assert sc["margin"] == pytest.approx(min(_gaps(want)), rel=1e-12)
+
+
+def test_hu_decision_margins_four_and_two_tours(oracle_mod):
+    """The g_min pick (four tours) and the two-tour branch of the HU step, by hand.
+    Four tours, 1 h of road each, areas [3, 2, 12, 8], rates 1..4 dealt one per tour:
+      T = 1 + A/R = [4, 2, 5, 3]; g_max t2 vs t0, t1, t3; g_max2 t0 vs t1, t3; g_min t1 vs t3
+      (scale 3); g_min keeps a single HU, so the round ends there.
+    Two tours, areas [10, 40], rates 1..4 dealt round robin: t0 {1, 3} R = 4, t1 {2, 4} R = 6;
+      T = [3.5, 1 + 40/6]; g_max t1 vs t0; with two tours g_min = g_max2 = t0 (no pick of its own),
+      and the acceptance test compares against T(g_min) after the trial move:
+      trial 1: T(t1) = 1 + 40/7 vs T(t0) = 1 + 10/3; 3 is the last: T(t0) = 11, stop: 11 vs 1 + 40/6."""
+    four = I.custom_instance([(0, 0), (20, 5), (5, 20), (-20, -5), (-5, -20), (20, 0), (0, 20), (-20, 0), (0, -20)],
+                             area=[3.0, 2.0, 12.0, 8.0], supply=[100.0] * 4, demand=[50.0] * 4,
+                             hu_rate=[1.0, 2.0, 3.0, 4.0], hu_speed=40.0, su_cap=[10.0] * 4, su_fill=[0.25] * 4,
+                             su_speed=[40.0] * 4, n_tours=4)
+    o = oracle_mod.Oracle(four)
+    rows, sc = o.decision_trace(oracle_mod.Plan.from_lists([[0], [1], [2], [3]], [[0], [1], [2], [3]]))
+    want = [("hu_max", 5, 4, 5), ("hu_max", 5, 2, 5), ("hu_max", 5, 3, 5),
+            ("hu_max2", 4, 2, 4), ("hu_max2", 4, 3, 4), ("hu_min", 2, 3, 3)]
+    _check_trace(rows, want)
+    assert sc["margin"] == pytest.approx(min(_gaps(want)), rel=1e-12)
+    two = I.custom_instance([(0, 0), (20, 5), (5, 20), (20, 0), (0, 20)], area=[10.0, 40.0], supply=[100.0] * 2,
+                            demand=[50.0] * 2, hu_rate=[1.0, 2.0, 3.0, 4.0], hu_speed=40.0, su_cap=[10.0] * 2,
+                            su_fill=[0.25] * 2, su_speed=[40.0] * 2, n_tours=2)
+    o2 = oracle_mod.Oracle(two)
+    rows, sc = o2.decision_trace(oracle_mod.Plan.from_lists([[0], [1]], [[0], [1]]))
+    want = [("hu_max", 1 + 40 / 6, 3.5, 1 + 40 / 6), ("hu_accept", 1 + 40 / 7, 1 + 10 / 3, 1 + 40 / 7),
+            ("hu_stop", 11, 1 + 40 / 6, 11)]
+    _check_trace(rows, want)
+    assert sc["tmax"] == pytest.approx(1 + 40 / 6, rel=1e-12)
+    assert sc["margin"] == pytest.approx(min(_gaps(want)), rel=1e-12)
+
+
+def test_gate_decision_margin(oracle_mod):
+    """The gate's gap compares Tmax with Tmax*, scaled by the larger (Sec. 2.5); without the
+    gate there is no such decision. One tour: no pick, so the gate is the only decision."""
+    o = oracle_mod.Oracle(_hand_one_tour())
+    plan = oracle_mod.Plan.from_lists([[0]], [[0, 1]])
+    rows, sc = o.decision_trace(plan, tmax_star=0.8, gate=1)
+    _check_trace(rows, [("gate", 0.75, 0.8, 0.8)])
+    assert sc["margin"] == pytest.approx(0.05 / 0.8, rel=1e-12)
+    rows, sc = o.decision_trace(plan, tmax_star=0.7, gate=2)
+    _check_trace(rows, [("gate", 0.75, 0.7, 0.75)])
+    assert math.isinf(sc["cost"])
+    rows, sc = o.decision_trace(plan, tmax_star=0.7, gate=0)
+    assert rows == [] and math.isinf(sc["margin"])
+
+
 def _su_trace_instance():
     # field-to-BP distances 15, 23.75, 60 km; SU speed 40 km/h -> round trips 0.75, 1.1875, 3 h
     xy = [(0, 0), (10, 15), (23.75, 10), (-10, -60), (10, 0), (0, 10), (-10, 0)]
@@ -214,6 +304,39 @@ def test_su_local_min_hand_trace(oracle_mod):
     assert list(s["su_tour"]) == [0, 1, 1, 0, 2, 2, 2, 1, 2]
     assert list(s["n_su"]) == [2, 3, 4]
     assert list(s["twait"]) == [0.625, 0.5625, 0.75]
+
+
+def test_su_decision_margins_hand_trace(oracle_mod):
+    """The decision gaps of the SU trace above (Algorithm 2, Eq. 6), derived by hand. The scale
+    of a tour's T_wait is |drive| + |fill|, the size of the two terms Eq. 6 subtracts (T_wait can be
+    near zero). A pick's gap is scaled by the larger of the two tours' scales; an acceptance test by
+    the larger of the trial g_max's scale and g_max2's; the termination test by the larger of the
+    new maximum's scale and the old g_max's. All values are dyadic, so they are exact.
+      R1: T_wait = [1/8, 5/16, 15/8], scales [11/8, 33/16, 33/8]; trials 1/8 -> 7/4 (scale 17/4)
+          and 4/8 -> 11/8 (37/8) against 5/16; stop: 1 (scale 5) vs 15/8.
+      R2: [5/8, 5/16, 1], scales [7/8, 33/16, 5]; trials 2/8 -> 3/4 (21/4), 5/8 -> 3/8 (45/8)
+          against 5/8; stop: 15/16 (23/16) vs 1 (5).
+      R3: [5/8, 15/16, 3/8], scales [7/8, 23/16, 45/8]; max t1; trial 3/8 -> 9/16 (29/16) against
+          5/8; stop: 3/4 (21/4) vs 15/16 (23/16).
+      R4: [5/8, 9/16, 3/4], scales [7/8, 29/16, 21/4]; trial 2/8 -> 1/2 (11/2) against 5/8;
+          stop: 13/16 (25/16) vs 3/4 (21/4): not lower, undone.
+    The HU step has three equal completion times (1.5 h each): ties, so no gap.
+    The margin is the smallest gap: (1/16)/(21/4) (R4, stop)."""
+    o = oracle_mod.Oracle(_su_trace_instance())
+    rows, sc = o.decision_trace(oracle_mod.Plan.from_lists([[0], [1], [2]], [[0], [1], [2]]))
+    want = [
+        ("su_max", 15 / 8, 1 / 8, 33 / 8), ("su_max", 15 / 8, 5 / 16, 33 / 8), ("su_max2", 5 / 16, 1 / 8, 33 / 16),
+        ("su_accept", 7 / 4, 5 / 16, 17 / 4), ("su_accept", 11 / 8, 5 / 16, 37 / 8), ("su_stop", 1, 15 / 8, 5),
+        ("su_max", 1, 5 / 8, 5), ("su_max", 1, 5 / 16, 5), ("su_max2", 5 / 8, 5 / 16, 33 / 16),
+        ("su_accept", 3 / 4, 5 / 8, 21 / 4), ("su_accept", 3 / 8, 5 / 8, 45 / 8), ("su_stop", 15 / 16, 1, 5),
+        ("su_max", 15 / 16, 5 / 8, 23 / 16), ("su_max", 15 / 16, 3 / 8, 45 / 8), ("su_max2", 5 / 8, 3 / 8, 45 / 8),
+        ("su_accept", 9 / 16, 5 / 8, 29 / 16), ("su_stop", 3 / 4, 15 / 16, 21 / 4),
+        ("su_max", 3 / 4, 5 / 8, 21 / 4), ("su_max", 3 / 4, 9 / 16, 21 / 4), ("su_max2", 5 / 8, 9 / 16, 29 / 16),
+        ("su_accept", 1 / 2, 5 / 8, 11 / 2), ("su_stop", 13 / 16, 3 / 4, 21 / 4),
+    ]
+    _check_trace(rows, want, rel=0)
+    assert sc["margin"] == (1 / 16) / (21 / 4)
+    assert sc["margin"] == min(_gaps(want))
 
 
 def test_init_hand_trace(oracle_mod):
