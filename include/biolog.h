@@ -164,6 +164,20 @@ int bl_plan_init_batch(const bl_instance *insts, int32_t n_inst, const bl_params
    errors (BL_ETIMEOUT) surface at the next synchronising call. */
 int bl_search_step(bl_handle *h, int32_t n_iters);
 
+/* Inspection of the search kernel itself (Steps 9-12 of Algorithm 1, the
+   three evaluation steps of Sec. 2.5): one iteration exactly as
+   bl_search_step runs it -- the same kernel, launch shape and work items,
+   with the argmin and the update of x_old, x*, C*, Tmax* -- that also writes
+   each candidate's result where the kernel decides it: d_out[2 (k stride +
+   i)] = C_i and d_out[2 (k stride + i) + 1] = Tmax_i for candidate i of
+   instance k. An infeasible candidate (Eq. 2) gets {+inf, +inf}; one the
+   completion-time gate discards {+inf, Tmax_i}; the rest {C_i, Tmax_i}.
+   d_out is device memory owned by the caller, at least 8 n_inst stride
+   bytes; stride >= the candidates per iteration. Asynchronous on the
+   handle's stream; not for timing (the search never writes d_out).
+   Errors: BL_EINVAL, BL_ESTATE, BL_ECUDA. */
+int bl_search_step_inspect(bl_handle *h, float *d_out, int32_t stride);
+
 /* Synchronise and report instance `inst`'s best plan x*, re-scored once for
    the per-tour table (Table 2's rows). */
 int bl_best_plan(bl_handle *h, int32_t inst, bl_plan *out);
@@ -188,9 +202,13 @@ int bl_get_log(bl_handle *h, int32_t inst, uint32_t first, int32_t n, int32_t *i
    Host outputs (any may be NULL): cost[n], tmax[n] (FP32; +inf when
    infeasible), moves[n x 4] ({kind, vertex, a, b}: kind 0 field reinsert
    (a = BP, b = slot), 1 BP reinsert (a = tour, b = slot), 2 field swap
-   (a = other field), 3 BP swap (a = other BP)), n_hu[n x T], n_su[n x T]. */
+   (a = other field), 3 BP swap (a = other BP)), n_hu[n x T], n_su[n x T],
+   and the HU and SU assignments the two local minimisations of Sec. 2.5
+   reach, hu_tour[n x H] and su_tour[n x S] (tour of each unit by id, -1
+   when unassigned: infeasible candidates). */
 int bl_score_candidates(bl_handle *h, int32_t inst, int32_t use_best, uint32_t iter, float tmax_star, int32_t i0,
-                        int32_t n, float *cost, float *tmax, int16_t *moves, int16_t *n_hu, int16_t *n_su);
+                        int32_t n, float *cost, float *tmax, int16_t *moves, int16_t *n_hu, int16_t *n_su,
+                        int16_t *hu_tour, int16_t *su_tour);
 
 /* Inspection: the decoded candidate plans (Step 8 applied to the base) for
    candidate indices idx[0..n-1]; plans is a host buffer of n x (2B+T+F)

@@ -1003,7 +1003,7 @@ int or_score_batch(const or_ctx *c, const or_params *prm, uint32_t iter,
                    const int16_t *bp_order, const int16_t *tour_cnt, const int16_t *field_order, const int16_t *bp_cnt,
                    double tmax_star, int32_t i0, int32_t n, int32_t nthreads,
                    double *cost, double *tmax, double *margin, int32_t *feasible, int16_t *moves,
-                   int32_t *n_hu, int32_t *n_su, double *ops_total)
+                   int32_t *n_hu, int32_t *n_su, int32_t *hu_tour, int32_t *su_tour, double *ops_total)
 {
     oplan base;
     plan_alloc(&base, c->T, c->B, c->F);
@@ -1025,7 +1025,8 @@ int or_score_batch(const or_ctx *c, const or_params *prm, uint32_t iter,
             apply_move(&base, mv, &cand);
             or_score r;
             or_detail det = {n_hu ? n_hu + (size_t)k * c->T : NULL, n_su ? n_su + (size_t)k * c->T : NULL,
-                             NULL, NULL, NULL, NULL, NULL};
+                             NULL, NULL, NULL, hu_tour ? hu_tour + (size_t)k * c->H : NULL,
+                             su_tour ? su_tour + (size_t)k * c->S : NULL};
             score_plan(c, prm, &cand, tmax_star, prm->gate, &r, &det);
             if (cost) cost[k] = r.cost;
             if (tmax) tmax[k] = r.tmax;
@@ -1082,7 +1083,7 @@ int or_search(const or_ctx *c, const or_params *prm, or_state *st, int32_t n_ite
         plan_copy(&base, use_best ? &xbest : &xold);
         plan_to_enc(&base, bo, tc, fo, bc);
         or_score_batch(c, prm, iter, bo, tc, fo, bc, st->tmaxstar, 0, n_cand, nthreads, cost, tmx, mrg,
-                       NULL, NULL, NULL, NULL, NULL);
+                       NULL, NULL, NULL, NULL, NULL, NULL, NULL);
         /* Step 13: i* = argmin C_i, ties to the lowest index */
         int32_t istar = 0;
         for (int32_t k = 1; k < n_cand; ++k) if (cost[k] < cost[istar]) istar = k;

@@ -100,7 +100,8 @@ def lib():
             L.or_validate_enc.argtypes = [C.c_int, C.c_int, C.c_int, i16p, i16p, i16p, i16p]
             vp = C.c_void_p
             L.or_score_batch.argtypes = [C.c_void_p, C.POINTER(Params), C.c_uint32, i16p, i16p, i16p, i16p,
-                                         C.c_double, C.c_int32, C.c_int32, C.c_int32, vp, vp, vp, vp, vp, vp, vp, vp]
+                                         C.c_double, C.c_int32, C.c_int32, C.c_int32, vp, vp, vp, vp, vp, vp, vp, vp,
+                                         vp, vp]
             L.or_search.argtypes = [C.c_void_p, C.POINTER(Params), C.POINTER(_State), C.c_int32, C.c_int32, C.c_int32,
                                     vp, vp, vp, vp, vp, vp, vp, vp, vp, vp]
             L.or_max_threads.restype = C.c_int
@@ -251,15 +252,17 @@ class Oracle:
         moves = np.zeros((n, 4), np.int16)
         n_hu = np.zeros((n, self.T), np.int32) if details else None
         n_su = np.zeros((n, self.T), np.int32) if details else None
+        hu = np.zeros((n, self.H), np.int32) if details else None
+        su = np.zeros((n, self.S), np.int32) if details else None
         ops = C.c_double(0.0)
         rc = lib().or_score_batch(self._h, C.byref(params), iter_, *base.arrays(), float(tmax_star), int(i0), int(n),
                                   int(threads), _p(cost), _p(tmax), _p(margin), _p(feas), _p(moves), _p(n_hu),
-                                  _p(n_su), C.cast(C.pointer(ops), C.c_void_p))
+                                  _p(n_su), _p(hu), _p(su), C.cast(C.pointer(ops), C.c_void_p))
         if rc:
             raise ValueError("bad plan")
         out = dict(cost=cost, tmax=tmax, margin=margin, feasible=feas.astype(bool), moves=moves, ops=ops.value)
         if details:
-            out.update(n_hu=n_hu, n_su=n_su)
+            out.update(n_hu=n_hu, n_su=n_su, hu_tour=hu, su_tour=su)
         return out
 
     def eps_select(self, params: Params, iter_: int) -> bool:

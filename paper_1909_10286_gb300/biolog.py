@@ -25,6 +25,7 @@ BL_OK, BL_EINVAL, BL_EINFEASIBLE_INSTANCE, BL_ETOO_LARGE, BL_ECUDA, BL_ETIMEOUT,
 EXPORTS = ("bl_workspace_bytes", "bl_plan_init", "bl_plan_init_batch", "bl_search_step", "bl_best_plan",
            "bl_get_state", "bl_set_state", "bl_get_log", "bl_score_candidates", "bl_decode_candidates",
            "bl_get_config", "bl_plan_free", "bl_last_error", "bl_global_error", "bl_argmin_noalloc", "bl_wait_selftest",
+           "bl_search_step_inspect",
            "bl_mlp_create", "bl_mlp_forward", "bl_mlp_grads", "bl_mlp_train_step", "bl_mlp_get", "bl_mlp_set",
            "bl_mlp_free", "bl_mlp_last_error", "bl_gemm_bf16", "bl_features", "bl_search_step_learned")
 
@@ -81,12 +82,13 @@ def load(path: str | None = None):
             L.bl_plan_init.argtypes = [C.POINTER(bl_instance), C.POINTER(bl_params), vp, C.POINTER(vp)]
             L.bl_plan_init_batch.argtypes = [C.POINTER(bl_instance), C.c_int32, C.POINTER(bl_params), vp, C.POINTER(vp)]
             L.bl_search_step.argtypes = [vp, C.c_int32]
+            L.bl_search_step_inspect.argtypes = [vp, vp, C.c_int32]
             L.bl_best_plan.argtypes = [vp, C.c_int32, C.POINTER(bl_plan)]
             L.bl_get_state.argtypes = [vp, C.c_int32, C.POINTER(bl_state)]
             L.bl_set_state.argtypes = [vp, C.c_int32, C.POINTER(bl_state)]
             L.bl_get_log.argtypes = [vp, C.c_int32, C.c_uint32, C.c_int32, vp, vp, vp, vp, vp]
             L.bl_score_candidates.argtypes = [vp, C.c_int32, C.c_int32, C.c_uint32, C.c_float, C.c_int32, C.c_int32,
-                                              vp, vp, vp, vp, vp]
+                                              vp, vp, vp, vp, vp, vp, vp]
             L.bl_decode_candidates.argtypes = [vp, C.c_int32, C.c_int32, C.c_uint32, vp, C.c_int32, vp]
             L.bl_get_config.argtypes = [vp, vp, vp, vp, vp, vp]
             L.bl_wait_selftest.argtypes = [vp, C.c_uint64, C.POINTER(C.c_uint64)]
@@ -182,6 +184,12 @@ class Search:
     def search_step(self, n_iters: int):
         _check(load().bl_search_step(self.h, int(n_iters)), self.h)
 
+    def search_step_inspect(self, out, stride: int):
+        """bl_search_step_inspect: one iteration of the search kernel that also writes {C_i, Tmax_i}
+        per candidate into `out`, a caller-owned float32 CUDA tensor of >= 2 * n_inst * stride values."""
+        assert out.is_cuda and out.dtype.itemsize == 4 and out.numel() >= 2 * len(self.instances) * stride
+        _check(load().bl_search_step_inspect(self.h, C.c_void_p(out.data_ptr()), int(stride)), self.h)
+
     def best_plan(self, inst: int = 0) -> dict:
         I = self.instances[inst]
         B, T, F, H, S = I.n_bps, I.n_tours, I.n_fields, I.n_hu, I.n_su
@@ -218,13 +226,17 @@ class Search:
         return o
 
     # --- inspection (parity tests)
-    def score_candidates(self, use_best: int, iter_: int, tmax_star: float, i0: int, n: int, inst: int = 0) -> dict:
-        T = self.instances[inst].n_tours
+    def score_candidates(self, use_best: int, iter_: int, tmax_star: float, i0: int, n: int, inst: int = 0,
+                         units: bool = False) -> dict:
+        I = self.instances[inst]
+        T = I.n_tours
         o = dict(cost=np.zeros(n, np.float32), tmax=np.zeros(n, np.float32), moves=np.zeros((n, 4), np.int16),
                  n_hu=np.zeros((n, T), np.int16), n_su=np.zeros((n, T), np.int16))
+        if units:
+            o.update(hu_tour=np.zeros((n, I.n_hu), np.int16), su_tour=np.zeros((n, I.n_su), np.int16))
         _check(load().bl_score_candidates(self.h, int(inst), int(use_best), int(iter_), float(tmax_star), int(i0),
                                           int(n), _p(o["cost"]), _p(o["tmax"]), _p(o["moves"]), _p(o["n_hu"]),
-                                          _p(o["n_su"])), self.h)
+                                          _p(o["n_su"]), _p(o.get("hu_tour")), _p(o.get("su_tour"))), self.h)
         return o
 
     def decode_candidates(self, use_best: int, iter_: int, idx, inst: int = 0) -> np.ndarray:

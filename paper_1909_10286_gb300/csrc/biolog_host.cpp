@@ -816,6 +816,23 @@ int bl_search_step(bl_handle *h, int32_t n_iters)
     return BL_OK;
 }
 
+int bl_search_step_inspect(bl_handle *h, float *d_out, int32_t stride)
+{
+    if (!h || !d_out) return BL_EINVAL;
+    if (h->failed) return BL_ESTATE;
+    int32_t n_max = 0;
+    for (const InstMeta &M : h->meta) n_max = std::max(n_max, M.n_cand);
+    if (stride < n_max) {
+        h->err = "bl_search_step_inspect: stride must be at least the candidates per iteration";
+        return BL_EINVAL;
+    }
+    CK(h, launch_search_iteration(h->cfg, h->at<InstMeta>(h->ws.meta), h->at<WorkItem>(h->ws.work),
+                                  (int32_t)h->work.size(), h->sp, h->at<unsigned long long>(h->ws.slot_key),
+                                  h->at<float>(h->ws.slot_tmax), h->at<int32_t>(h->ws.slot_base), h->stream, nullptr,
+                                  nullptr, 0, reinterpret_cast<float2 *>(d_out), stride));
+    return BL_OK;
+}
+
 int bl_get_state(bl_handle *h, int32_t inst, bl_state *out)
 {
     if (!h || !out || inst < 0 || inst >= h->n_inst) return BL_EINVAL;
@@ -913,12 +930,15 @@ int bl_get_log(bl_handle *h, int32_t inst, uint32_t first, int32_t n, int32_t *i
 }
 
 int bl_score_candidates(bl_handle *h, int32_t inst, int32_t use_best, uint32_t iter, float tmax_star, int32_t i0,
-                        int32_t n, float *cost, float *tmax, int16_t *moves, int16_t *n_hu, int16_t *n_su)
+                        int32_t n, float *cost, float *tmax, int16_t *moves, int16_t *n_hu, int16_t *n_su,
+                        int16_t *hu_tour, int16_t *su_tour)
 {
     if (!h || inst < 0 || inst >= h->n_inst || n < 0 || i0 < 0) return BL_EINVAL;
     if (h->failed) return BL_ESTATE;
-    const int T = h->insts[(size_t)inst].T;
-    const size_t per = 4 + 4 + 8 + 4 * (size_t)T;
+    const HostInst &hi = h->insts[(size_t)inst];
+    const int T = hi.T, H = hi.H, S = hi.S;
+    const size_t nh = hu_tour ? (size_t)H : 0, ns = su_tour ? (size_t)S : 0;
+    const size_t per = 4 + 4 + 8 + 4 * (size_t)T + 2 * (nh + ns) + 16;
     const int chunk = (int)((kScratchBytes - 1024) / per);
     unsigned char *s = h->at<unsigned char>(h->ws.scratch);
     for (int k0 = 0; k0 < n; k0 += chunk) {
@@ -928,13 +948,19 @@ int bl_score_candidates(bl_handle *h, int32_t inst, int32_t use_best, uint32_t i
         int16_t *dm = (int16_t *)(dt + m);
         int16_t *dh = dm + 4 * (size_t)m;
         int16_t *ds = dh + (size_t)m * T;
+        int16_t *dhu = hu_tour ? ds + (size_t)m * T : nullptr;
+        int16_t *dsu = su_tour ? ds + (size_t)m * T + (size_t)m * nh : nullptr;
         CK(h, launch_score_dump(h->cfg, h->at<InstMeta>(h->ws.meta), inst, use_best, iter, tmax_star, i0 + k0, m, 0,
-                                h->sp, dc, dt, dm, dh, ds, nullptr, nullptr, nullptr, nullptr, nullptr, h->stream));
+                                h->sp, dc, dt, dm, dh, ds, nullptr, nullptr, nullptr, dhu, dsu, h->stream));
         if (cost) CK(h, cudaMemcpyAsync(cost + k0, dc, 4 * (size_t)m, cudaMemcpyDeviceToHost, h->stream));
         if (tmax) CK(h, cudaMemcpyAsync(tmax + k0, dt, 4 * (size_t)m, cudaMemcpyDeviceToHost, h->stream));
         if (moves) CK(h, cudaMemcpyAsync(moves + 4 * (size_t)k0, dm, 8 * (size_t)m, cudaMemcpyDeviceToHost, h->stream));
         if (n_hu) CK(h, cudaMemcpyAsync(n_hu + (size_t)k0 * T, dh, 2 * (size_t)m * T, cudaMemcpyDeviceToHost, h->stream));
         if (n_su) CK(h, cudaMemcpyAsync(n_su + (size_t)k0 * T, ds, 2 * (size_t)m * T, cudaMemcpyDeviceToHost, h->stream));
+        if (hu_tour)
+            CK(h, cudaMemcpyAsync(hu_tour + (size_t)k0 * H, dhu, 2 * (size_t)m * H, cudaMemcpyDeviceToHost, h->stream));
+        if (su_tour)
+            CK(h, cudaMemcpyAsync(su_tour + (size_t)k0 * S, dsu, 2 * (size_t)m * S, cudaMemcpyDeviceToHost, h->stream));
         CK(h, cudaStreamSynchronize(h->stream));
     }
     return BL_OK;

@@ -120,7 +120,7 @@ cudaError_t launch_search_iteration(const LaunchCfg &cfg, const InstMeta *d_meta
                                     int32_t n_work, SearchParams prm, unsigned long long *slot_key,
                                     float *slot_tmax, const int32_t *slot_base, cudaStream_t s,
                                     const uint32_t *cand_list = nullptr, const int32_t *cand_count = nullptr,
-                                    int32_t list_stride = 0);
+                                    int32_t list_stride = 0, float2 *insp = nullptr, int32_t insp_stride = 0);
 constexpr int NFEAT = 64;   // features per candidate move
 cudaError_t launch_features(const LaunchCfg &cfg, const InstMeta *d_meta, int32_t inst, int32_t use_best,
                             uint32_t iter, int32_t i0, int32_t n, SearchParams prm, uint16_t *d_feat,

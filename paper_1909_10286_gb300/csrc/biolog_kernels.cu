@@ -1314,7 +1314,8 @@ __global__ void __launch_bounds__(SH::NT, SH::MINB) search_iteration_kernel(cons
                                                                   const int32_t *__restrict__ slot_base,
                                                                   const uint32_t *__restrict__ cand_list,
                                                                   const int32_t *__restrict__ cand_count,
-                                                                  int32_t list_stride)
+                                                                  int32_t list_stride, float2 *__restrict__ insp,
+                                                                  int32_t insp_stride)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ BlockShared bs;
@@ -1356,6 +1357,8 @@ __global__ void __launch_bounds__(SH::NT, SH::MINB) search_iteration_kernel(cons
         const long long c0l = (long long)wi.tile_idx * tl;
         const int c0 = (int)min(c0l, cend);
         const int c1 = (int)min(c0l + tl, cend);
+        // inspection (off in the timed path): {C_i, Tmax_i} of candidate i where it is decided
+        float2 *const ins = insp ? insp + (size_t)wi.inst * insp_stride : nullptr;
         unsigned long long best = ~0ull;
         float best_t = 0.f;
         // each warp: draw 32 moves at a time and queue the feasible ones (Eq. 2); take 32 queued
@@ -1399,6 +1402,7 @@ __global__ void __launch_bounds__(SH::NT, SH::MINB) search_iteration_kernel(cons
                     if (!feas) {
                         const unsigned long long k = make_key(__int_as_float(0x7f800000), (uint32_t)i);
                         if (k < best) { best = k; best_t = __int_as_float(0x7f800000); }
+                        if (ins) ins[i] = make_float2(__int_as_float(0x7f800000), __int_as_float(0x7f800000));
                     }
                 }
                 const unsigned ball = __ballot_sync(0xffffffffu, feas);
@@ -1431,6 +1435,7 @@ __global__ void __launch_bounds__(SH::NT, SH::MINB) search_iteration_kernel(cons
                     if (isinf(r1.cost)) {   // discarded by the gate: C = +inf (Sec. 2.5)
                         const unsigned long long k = make_key(r1.cost, (uint32_t)i);
                         if (k < best) { best = k; best_t = r1.tmax; }
+                        if (ins) ins[i] = make_float2(r1.cost, r1.tmax);
                     } else {
                         kept = true;
                     }
@@ -1479,6 +1484,7 @@ __global__ void __launch_bounds__(SH::NT, SH::MINB) search_iteration_kernel(cons
                                                        nullptr, nullptr, nullptr, nullptr);
                     const unsigned long long k = make_key(r.cost, (uint32_t)i);
                     if (k < best) { best = k; best_t = r.tmax; }
+                    if (ins) ins[i] = make_float2(r.cost, r.tmax);
                 }
                 __syncwarp();
                 q2head = (q2head + take2) & (WQ - 1);
@@ -1956,7 +1962,8 @@ template <class SH, int L>
 __global__ void __launch_bounds__(COOP_NT) search_iteration_coop_kernel(
     const InstMeta *__restrict__ meta, const WorkItem *__restrict__ work, int32_t n_work, SearchParams prm, SmemPlan sp,
     unsigned long long *__restrict__ slot_key, float *__restrict__ slot_tmax, const int32_t *__restrict__ slot_base,
-    const uint32_t *__restrict__ cand_list, const int32_t *__restrict__ cand_count, int32_t list_stride)
+    const uint32_t *__restrict__ cand_list, const int32_t *__restrict__ cand_count, int32_t list_stride,
+    float2 *__restrict__ insp, int32_t insp_stride)
 {
     static_assert(L >= SH::MAXT && L <= 32 && (32 % L) == 0, "one lane per tour, groups inside a warp");
     extern __shared__ __align__(16) unsigned char smem[];
@@ -1991,6 +1998,7 @@ __global__ void __launch_bounds__(COOP_NT) search_iteration_coop_kernel(
         const long long c0l = (long long)wi.tile_idx * tl;
         const int c0 = (int)min(c0l, cend);
         const int c1 = (int)min(c0l + tl, cend);
+        float2 *const ins = insp ? insp + (size_t)wi.inst * insp_stride : nullptr;
         unsigned long long best = ~0ull;
         float best_t = 0.f;
         for (int pos = c0 + grp; pos < c1; pos += NG) {
@@ -2006,6 +2014,7 @@ __global__ void __launch_bounds__(COOP_NT) search_iteration_coop_kernel(
                 k = make_key(__int_as_float(0x7f800000), (uint32_t)i);
             }
             if (k < best) { best = k; best_t = t; }
+            if (ins && gl == 0) ins[i] = make_float2(__uint_as_float((uint32_t)(k >> 32)), t);
         }
         block_argmin_finalize<COOP_NT>(best, best_t, bs, M, wi, slot_key, slot_tmax, slot_base, c, prm, iter);
     }
@@ -2676,13 +2685,13 @@ int search_blocks_per_sm(int32_t shape, size_t smem)
 cudaError_t launch_search_iteration(const LaunchCfg &cfg, const InstMeta *d_meta, const WorkItem *d_work,
                                     int32_t n_work, SearchParams prm, unsigned long long *slot_key, float *slot_tmax,
                                     const int32_t *slot_base, cudaStream_t s, const uint32_t *cand_list,
-                                    const int32_t *cand_count, int32_t list_stride)
+                                    const int32_t *cand_count, int32_t list_stride, float2 *insp, int32_t insp_stride)
 {
     if (cfg.lanes > 1) {
         const SmemPlan cp = coop_plan_for(cfg);
         const cudaError_t e = with_coop_kernel(cfg.shape, cfg.lanes, [&](auto kern) {
             kern<<<cfg.grid, COOP_NT, cp.total, s>>>(d_meta, d_work, n_work, prm, cp, slot_key, slot_tmax, slot_base,
-                                                     cand_list, cand_count, list_stride);
+                                                     cand_list, cand_count, list_stride, insp, insp_stride);
             return cudaSuccess;
         });
         if (e != cudaSuccess) return e;
@@ -2692,19 +2701,23 @@ cudaError_t launch_search_iteration(const LaunchCfg &cfg, const InstMeta *d_meta
     switch (cfg.shape) {
     case SHAPE_T4_S64_DSMEM:
         search_iteration_kernel<ShapeA><<<cfg.grid, ShapeA::NT, sp.total, s>>>(
-            d_meta, d_work, n_work, prm, sp, slot_key, slot_tmax, slot_base, cand_list, cand_count, list_stride);
+            d_meta, d_work, n_work, prm, sp, slot_key, slot_tmax, slot_base, cand_list, cand_count, list_stride, insp,
+            insp_stride);
         break;
     case SHAPE_T6_S64_GMEM:
         search_iteration_kernel<ShapeB><<<cfg.grid, ShapeB::NT, sp.total, s>>>(
-            d_meta, d_work, n_work, prm, sp, slot_key, slot_tmax, slot_base, cand_list, cand_count, list_stride);
+            d_meta, d_work, n_work, prm, sp, slot_key, slot_tmax, slot_base, cand_list, cand_count, list_stride, insp,
+            insp_stride);
         break;
     case SHAPE_T10_S128_GMEM:
         search_iteration_kernel<ShapeD><<<cfg.grid, ShapeD::NT, sp.total, s>>>(
-            d_meta, d_work, n_work, prm, sp, slot_key, slot_tmax, slot_base, cand_list, cand_count, list_stride);
+            d_meta, d_work, n_work, prm, sp, slot_key, slot_tmax, slot_base, cand_list, cand_count, list_stride, insp,
+            insp_stride);
         break;
     default:
         search_iteration_kernel<ShapeC><<<cfg.grid, ShapeC::NT, sp.total, s>>>(
-            d_meta, d_work, n_work, prm, sp, slot_key, slot_tmax, slot_base, cand_list, cand_count, list_stride);
+            d_meta, d_work, n_work, prm, sp, slot_key, slot_tmax, slot_base, cand_list, cand_count, list_stride, insp,
+            insp_stride);
     }
     return cudaGetLastError();
 }
