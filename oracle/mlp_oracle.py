@@ -57,3 +57,96 @@ def grads(params, x, t):
     gb1 = dz1.sum(0)
     loss = float(np.mean((y - t) ** 2))
     return [gw1, gb1, gw2, gb2, gw3, gb3, gw4, gb4], loss
+
+
+# ---------------------------------------------------------------------------
+# Gradients at the rounding points of the tensor-core training pass, with a
+# bound per entry. The training pass keeps BF16 copies of the three GEMM
+# weight matrices, rounds every hidden activation to BF16 after its ReLU,
+# rounds the head's dz = dy * w4 and each dh = dz W to BF16 before the ReLU
+# mask, and accumulates every sum in FP32. The reference below takes the same
+# rounding points in FP64 arithmetic. Its bound follows each value as an
+# interval: an FP32 sum of K terms is off by at most 2 K 2^-24 times the sum
+# of their magnitudes, upstream errors propagate through the magnitudes, and
+# since round-to-nearest and ReLU are monotonic, a BF16 rounding of a value
+# known to within e lies between the roundings of the interval's ends -- it is
+# exactly the reference's unless the interval straddles a rounding boundary.
+# ---------------------------------------------------------------------------
+U32 = 2.0 ** -24
+
+
+def _round_interval(z, ez, relu=False):
+    f = (lambda v: np.maximum(v, 0.0)) if relu else (lambda v: v)  # noqa: E731
+    r = bf16(f(z))
+    lo, hi = bf16(f(z - ez)), bf16(f(z + ez))
+    return r, np.maximum(hi - r, r - lo)
+
+
+def _mask(v, ev, h, eh):
+    """v masked by h > 0 (ReLU backward), where h is known to within eh."""
+    on = h - eh > 0                      # surely positive on both sides
+    off = (h == 0) & (eh == 0)           # surely zero
+    unsure = ~on & ~off
+    out = np.where(on, v, 0.0)
+    err = np.where(on, ev, 0.0)
+    out = np.where(unsure & (h > 0), v, out)
+    err = np.where(unsure, np.abs(v) + ev, err)
+    return out, err
+
+
+def grads_bf16(params, x, t, acts=None):
+    """Gradients of mean((y - t)^2) at the training pass's rounding points (BF16 weights, BF16
+    activations and BF16 dz / dh; x taken as given), and an absolute bound per entry on how far an
+    FP32-accumulating pass with those rounding points can be from them. `acts` (optional): the
+    three BF16 hidden activations of the pass being checked, taken as exact -- then the bound
+    covers the backward pass alone, with that pass's own ReLU masks. Returns (grads, bounds, loss)
+    with grads and bounds in the parameter order w1, b1, w2, b2, w3, b3, w4, b4."""
+    w1, b1, w2, b2, w3, b3, w4, b4 = [np.asarray(p, dtype=np.float64) for p in params]
+    x = np.asarray(x, dtype=np.float64)
+    t = np.asarray(t, dtype=np.float64)
+    W = [bf16(w1), bf16(w2), bf16(w3)]
+    Bs = [b1, b2, b3]
+    M = x.shape[0]
+    a, ea = x, np.zeros_like(x)
+    hs, ehs = [], []
+    for l in range(3):
+        if acts is not None:
+            a, ea = np.asarray(acts[l], dtype=np.float64), np.zeros(acts[l].shape)
+            assert np.array_equal(bf16(a), a), "activations must be BF16 values"
+        else:
+            K = a.shape[1]
+            z = a @ W[l].T + Bs[l]
+            ez = 2 * K * U32 * (np.abs(a) @ np.abs(W[l]).T + np.abs(Bs[l])) + ea @ np.abs(W[l]).T
+            a, ea = _round_interval(z, ez, relu=True)
+        hs.append(a)
+        ehs.append(ea)
+    h3, eh3 = hs[2], ehs[2]
+    H = h3.shape[1]
+    y = h3 @ w4 + b4[0]
+    ey = 2 * H * U32 * (np.abs(h3) @ np.abs(w4) + abs(b4[0])) + eh3 @ np.abs(w4)
+    dy = 2.0 * (y - t) / M
+    edy = 2.0 * ey / M + 4 * U32 * np.abs(dy)
+    loss = float(np.mean((y - t) ** 2))
+    gw4 = h3.T @ dy
+    egw4 = np.abs(h3).T @ edy + eh3.T @ np.abs(dy) + 2 * M * U32 * (np.abs(h3).T @ np.abs(dy))
+    gb4 = np.array([dy.sum()])
+    egb4 = np.array([edy.sum() + 2 * M * U32 * np.abs(dy).sum()])
+    pre = np.outer(dy, w4)
+    dz, edz = _round_interval(pre, np.outer(edy, np.abs(w4)) + U32 * np.abs(pre))
+    dz, edz = _mask(dz, edz, h3, eh3)
+    acts, eacts = [x, hs[0], hs[1]], [np.zeros_like(x), ehs[0], ehs[1]]
+    gw, egw, gb, egb = [None] * 3, [None] * 3, [None] * 3, [None] * 3
+    for l in (2, 1, 0):
+        a, ea = acts[l], eacts[l]
+        gw[l] = dz.T @ a
+        egw[l] = np.abs(dz).T @ ea + edz.T @ np.abs(a) + 2 * M * U32 * (np.abs(dz).T @ np.abs(a))
+        gb[l] = dz.sum(0)
+        egb[l] = edz.sum(0) + 2 * M * U32 * np.abs(dz).sum(0)
+        if l > 0:
+            pre = dz @ W[l]
+            epre = edz @ np.abs(W[l]) + 2 * H * U32 * (np.abs(dz) @ np.abs(W[l]))
+            d, ed = _round_interval(pre, epre)
+            dz, edz = _mask(d, ed, hs[l - 1], ehs[l - 1])
+    grads = [gw[0], gb[0], gw[1], gb[1], gw[2], gb[2], gw4, gb4]
+    bounds = [egw[0], egb[0], egw[1], egb[1], egw[2], egb[2], egw4, egb4]
+    return grads, bounds, loss

@@ -82,3 +82,63 @@ def test_forward_bf16_rounds_only_the_hidden_layers():
     assert all(np.array_equal(R.bf16(h), h) for h in (h1, h2, h3))
     assert not np.array_equal(y2, yb2) and np.allclose(y2, yb2, rtol=0.05, atol=0.05)
     assert np.array_equal(h1, R.bf16(np.maximum(x2 @ p2[0].T + p2[1], 0)))
+
+
+def test_dyadic_case_is_exact():
+    """On the dyadic case every rounding point of the training pass is exact: the BF16-point
+    reference equals the plain FP64 backprop (pinned above by central differences) and an FP32
+    pass in numpy's summation order, bit for bit -- so the GPU's gradients must too."""
+    import mlp_cases as MC
+
+    for M in (512, 4096):
+        p, x, t = MC.dyadic_case(M=M)
+        g, _, loss = R.grads_bf16(p, x, t)
+        plain = [R.bf16(p[0]), p[1], R.bf16(p[2]), p[3], R.bf16(p[4]), p[5], p[6], p[7]]
+        gp, lp = R.grads(plain, x, t)
+        hs, g32 = MC.fp32_pass(p, x, t)
+        assert loss == lp
+        for k in range(8):
+            assert np.array_equal(g[k], gp[k]), k
+            assert np.array_equal(g32[k].astype(np.float64), g[k]), k
+            assert np.count_nonzero(g[k]) >= 0.4 * g[k].size, k   # not a trivially zero gradient
+        _, hr = R.forward_bf16(p, x)
+        assert all(np.array_equal(a.astype(np.float64), b) for a, b in zip(hs, hr))
+
+
+def test_bf16_bound_covers_an_fp32_pass():
+    """The per-entry bound of grads_bf16, given the activations of the pass it checks, covers an
+    FP32 pass with the training kernels' rounding points on random values, and is tight for the
+    layers next to the head (below 1 % of the entry for most of them)."""
+    import mlp_cases as MC
+
+    p, x, t = MC.random_case()
+    hs, g32 = MC.fp32_pass(p, x, t)
+    g, E, _ = R.grads_bf16(p, x, t, acts=hs)
+    for k in range(8):
+        assert np.all(np.abs(g32[k] - g[k]) <= E[k]), k
+    for k in (4, 5, 6, 7):
+        nz = g[k] != 0
+        assert np.median(E[k][nz] / np.abs(g[k][nz])) < 1e-2, k
+
+
+def test_bf16_bound_catches_planted_mistakes():
+    """Mistakes planted in the reference's gradients on the CPU -- a row of dW3 with the wrong sign,
+    three entries of db3 5 % off, one unit's db2 zeroed, dW2 scaled by 2 -- fall outside the bound
+    against a correct FP32 pass."""
+    import mlp_cases as MC
+
+    p, x, t = MC.random_case()
+    hs, g32 = MC.fp32_pass(p, x, t)
+    g, E, _ = R.grads_bf16(p, x, t, acts=hs)
+
+    def outside(k, gm):
+        return np.abs(g32[k] - gm) > E[k]
+
+    row = int(np.argmax(np.abs(g[4]).sum(1)))
+    gm = g[4].copy(); gm[row] *= -1
+    assert outside(4, gm)[row].mean() > 0.9
+    gm = g[5].copy(); j = np.argsort(-np.abs(g[5]))[:3]; gm[j] *= 1.05
+    assert outside(5, gm)[j].all()
+    gm = g[3].copy(); u = int(np.argmax(np.abs(g[3]))); gm[u] = 0.0
+    assert outside(3, gm)[u]
+    assert outside(2, 2 * g[2]).mean() > 0.5
