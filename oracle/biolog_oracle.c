@@ -95,6 +95,7 @@ typedef struct {
     int32_t fix_field_bp;  /* Sec. 2.6: a removed field goes back into its own BP */
     int32_t fix_resources; /* Case 2: keep the initial HU/SU dealing, no local minimisation */
     int32_t gate;          /* 0 off, 1 discard Tmax > Tmax*, 2 discard Tmax >= Tmax* */
+    int32_t k_moves;       /* Step 8 repeated: moves chained per candidate (0 or 1: one move) */
 } or_params;
 
 typedef struct {
@@ -387,11 +388,16 @@ static void init_plan(const or_ctx *c, oplan *p)
 /* Move record: {kind, vertex, a, b}: kind 0 field reinsert (a = BP,         */
 /* b = slot), 1 BP reinsert (a = tour, b = slot), 2 field swap (a = field),  */
 /* 3 BP swap (a = BP).                                                       */
+/* Repeating Step 8 (Sec. 2.5 mentions doing it a second time): move j of a  */
+/* candidate is drawn on the plan the first j moves made, from counter word  */
+/* 3 = 0 for j = 0 and j + 1 after (word 3 = 1 is the eps rule's counter).   */
 /* ------------------------------------------------------------------------ */
-static void draw_move(const or_ctx *c, const or_params *prm, uint32_t iter, uint32_t i,
+static uint32_t move_word3(int j) { return j == 0 ? 0u : (uint32_t)j + 1u; }
+
+static void draw_move(const or_ctx *c, const or_params *prm, uint32_t iter, uint32_t i, int j,
                       const oplan *base, int16_t mv[4])
 {
-    uint32_t ctr[4] = {i, iter, prm->inst_idx, 0u};
+    uint32_t ctr[4] = {i, iter, prm->inst_idx, move_word3(j)};
     uint32_t key[2] = {(uint32_t)prm->seed, (uint32_t)(prm->seed >> 32)};
     uint32_t r[4];
     or_philox4x32_10(ctr, key, r);
@@ -473,6 +479,26 @@ static void apply_move(const oplan *base, const int16_t mv[4], oplan *out)
                 if (out->tbp[g * B + j] == w) pw = &out->tbp[g * B + j];
             }
         *pv = w; *pw = v;
+    }
+}
+
+static int n_moves(const or_params *prm)
+{
+    if (prm->k_moves > 8) { fprintf(stderr, "oracle: at most 8 chained moves\n"); abort(); }
+    return prm->k_moves > 1 ? prm->k_moves : 1;
+}
+
+/* Candidate i of iteration `iter`: Step 8 applied k times, move j drawn on the
+   plan after the first j moves (a materialised list each time); mv receives
+   the k move records (4 words each). `scratch` is a plan of the same sizes. */
+static void make_candidate(const or_ctx *c, const or_params *prm, uint32_t iter, uint32_t i, const oplan *base,
+                           oplan *out, oplan *scratch, int16_t *mv)
+{
+    plan_copy(out, base);
+    for (int j = 0; j < n_moves(prm); ++j) {
+        draw_move(c, prm, iter, i, j, out, mv + 4 * j);
+        plan_copy(scratch, out);
+        apply_move(scratch, mv + 4 * j, out);
     }
 }
 
@@ -897,9 +923,26 @@ int or_move(const or_ctx *c, const or_params *prm, uint32_t iter, uint32_t i,
     oplan p;
     plan_alloc(&p, c->T, c->B, c->F);
     if (plan_from_enc(&p, bp_order, tour_cnt, field_order, bp_cnt)) { plan_release(&p); return -1; }
-    draw_move(c, prm, iter, i, &p, mv);
+    draw_move(c, prm, iter, i, 0, &p, mv);
     plan_release(&p);
     return 0;
+}
+
+/* Candidate i of iteration `iter` drawn from the plan given: its plan (encoding
+   into o_*) and its k move records (mv, 4 k words). */
+int or_candidate(const or_ctx *c, const or_params *prm, uint32_t iter, uint32_t i,
+                 const int16_t *bp_order, const int16_t *tour_cnt, const int16_t *field_order, const int16_t *bp_cnt,
+                 int16_t *mv, int16_t *o_bp_order, int16_t *o_tour_cnt, int16_t *o_field_order, int16_t *o_bp_cnt)
+{
+    oplan p, q, r;
+    plan_alloc(&p, c->T, c->B, c->F); plan_alloc(&q, c->T, c->B, c->F); plan_alloc(&r, c->T, c->B, c->F);
+    int rc = plan_from_enc(&p, bp_order, tour_cnt, field_order, bp_cnt);
+    if (!rc) {
+        make_candidate(c, prm, iter, i, &p, &q, &r, mv);
+        plan_to_enc(&q, o_bp_order, o_tour_cnt, o_field_order, o_bp_cnt);
+    }
+    plan_release(&p); plan_release(&q); plan_release(&r);
+    return rc ? -1 : 0;
 }
 
 int or_apply(const or_ctx *c, const int16_t *bp_order, const int16_t *tour_cnt, const int16_t *field_order,
@@ -1014,15 +1057,16 @@ int or_score_batch(const or_ctx *c, const or_params *prm, uint32_t iter,
 #pragma omp parallel reduction(+ : ops_sum)
 #endif
     {
-        oplan cand;
+        oplan cand, tmp;
         plan_alloc(&cand, c->T, c->B, c->F);
+        plan_alloc(&tmp, c->T, c->B, c->F);
+        const int km = n_moves(prm);
 #ifdef _OPENMP
 #pragma omp for schedule(dynamic, 64)
 #endif
         for (int32_t k = 0; k < n; ++k) {
-            int16_t mv[4];
-            draw_move(c, prm, iter, (uint32_t)(i0 + k), &base, mv);
-            apply_move(&base, mv, &cand);
+            int16_t mv[4 * 8];
+            make_candidate(c, prm, iter, (uint32_t)(i0 + k), &base, &cand, &tmp, mv);
             or_score r;
             or_detail det = {n_hu ? n_hu + (size_t)k * c->T : NULL, n_su ? n_su + (size_t)k * c->T : NULL,
                              NULL, NULL, NULL, hu_tour ? hu_tour + (size_t)k * c->H : NULL,
@@ -1032,10 +1076,11 @@ int or_score_batch(const or_ctx *c, const or_params *prm, uint32_t iter,
             if (tmax) tmax[k] = r.tmax;
             if (margin) margin[k] = r.margin;
             if (feasible) feasible[k] = r.feasible;
-            if (moves) memcpy(moves + (size_t)k * 4, mv, sizeof(mv));
+            if (moves) memcpy(moves + (size_t)k * 4 * km, mv, sizeof(int16_t) * 4 * (size_t)km);
             ops_sum += r.ops;
         }
         plan_release(&cand);
+        plan_release(&tmp);
     }
     if (ops_total) *ops_total = ops_sum;
     plan_release(&base);
@@ -1095,11 +1140,10 @@ int or_search(const or_ctx *c, const or_params *prm, or_state *st, int32_t n_ite
         if (force_istar && force_istar[it] >= 0 && force_istar[it] < n_cand) istar = force_istar[it];
         if (c_follow_o) c_follow_o[it] = cost[istar];
         int ind = 0;
-        int16_t mv[4];
-        draw_move(c, prm, iter, (uint32_t)istar, &base, mv);
+        int16_t mv[4 * 8];
+        make_candidate(c, prm, iter, (uint32_t)istar, &base, &cand, &xold, mv);
         if (isfinite(cost[istar])) {
             /* Steps 13-16: rebuild x_{i*}; update x*, C*; x_old <- x_{i*} */
-            apply_move(&base, mv, &cand);
             plan_copy(&xold, &cand);
             if (cost[istar] < st->cstar) {
                 plan_copy(&xbest, &cand);

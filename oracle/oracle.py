@@ -51,7 +51,8 @@ class _InstIn(C.Structure):
 
 class Params(C.Structure):
     _fields_ = [("eps", C.c_double), ("p_swap", C.c_double), ("seed", C.c_uint64), ("inst_idx", C.c_uint32),
-                ("fix_field_bp", C.c_int32), ("fix_resources", C.c_int32), ("gate", C.c_int32)]
+                ("fix_field_bp", C.c_int32), ("fix_resources", C.c_int32), ("gate", C.c_int32),
+                ("k_moves", C.c_int32)]
 
 
 class _Score(C.Structure):
@@ -91,6 +92,8 @@ def lib():
             L.or_init_plan.argtypes = [C.c_void_p, i16p, i16p, i16p, i16p]
             L.or_move.argtypes = [C.c_void_p, C.POINTER(Params), C.c_uint32, C.c_uint32, i16p, i16p, i16p, i16p, i16p]
             L.or_apply.argtypes = [C.c_void_p, i16p, i16p, i16p, i16p, i16p, i16p, i16p, i16p, i16p]
+            L.or_candidate.argtypes = [C.c_void_p, C.POINTER(Params), C.c_uint32, C.c_uint32, i16p, i16p, i16p, i16p,
+                                       i16p, i16p, i16p, i16p, i16p]
             L.or_score_plan.argtypes = [C.c_void_p, C.POINTER(Params), i16p, i16p, i16p, i16p, C.c_double, C.c_int32,
                                         C.POINTER(_Score), i32p, i32p, f64p, f64p, f64p, i32p, i32p]
             L.or_score_plan_trace.argtypes = [C.c_void_p, C.POINTER(Params), i16p, i16p, i16p, i16p, C.c_double,
@@ -154,9 +157,11 @@ class Plan:
         return tours, bps
 
 
-def make_params(eps=0.5, seed=0, inst_idx=0, fix_field_bp=0, fix_resources=0, gate=1, p_swap=0.0) -> Params:
+def make_params(eps=0.5, seed=0, inst_idx=0, fix_field_bp=0, fix_resources=0, gate=1, p_swap=0.0,
+                k_moves=1) -> Params:
+    assert 1 <= k_moves <= 8
     return Params(float(np.float32(eps)), float(np.float32(p_swap)), int(seed), int(inst_idx), int(fix_field_bp),
-                  int(fix_resources), int(gate))
+                  int(fix_resources), int(gate), int(k_moves))
 
 
 class Oracle:
@@ -202,6 +207,16 @@ class Oracle:
         if rc:
             raise ValueError("bad plan")
         return mv
+
+    def candidate(self, params: Params, iter_: int, i: int, base: Plan):
+        """Candidate i (Step 8 applied params.k_moves times): its plan and its k x 4 move records."""
+        k = max(1, params.k_moves)
+        mv = np.zeros(4 * k, dtype=np.int16)
+        out = Plan(np.zeros(self.B), np.zeros(self.T), np.zeros(self.F), np.zeros(self.B))
+        rc = lib().or_candidate(self._h, C.byref(params), iter_, i, *base.arrays(), mv, *out.arrays())
+        if rc:
+            raise ValueError("bad plan")
+        return out, mv.reshape(k, 4)
 
     def apply(self, base: Plan, mv) -> Plan:
         out = Plan(np.zeros(self.B), np.zeros(self.T), np.zeros(self.F), np.zeros(self.B))
@@ -249,7 +264,7 @@ class Oracle:
     def score_batch(self, params: Params, iter_: int, base: Plan, n: int, tmax_star=np.inf, i0=0, threads=1,
                     details=False) -> dict:
         cost = np.zeros(n); tmax = np.zeros(n); margin = np.zeros(n); feas = np.zeros(n, np.int32)
-        moves = np.zeros((n, 4), np.int16)
+        moves = np.zeros((n, 4 * max(1, params.k_moves)), np.int16)
         n_hu = np.zeros((n, self.T), np.int32) if details else None
         n_su = np.zeros((n, self.T), np.int32) if details else None
         hu = np.zeros((n, self.H), np.int32) if details else None

@@ -146,6 +146,49 @@ def test_sampled_moves_cover_the_neighbourhood(oracle_mod):
     assert r["cost"].min() == best_nbh
 
 
+def test_two_move_candidates_reach_the_two_step_neighbourhood(oracle_mod):
+    """Candidates of two chained moves (Step 8 repeated) reach exactly the plans two reinsert moves
+    away -- the one-move neighbourhood of every one-move neighbour, built with plain list operations
+    (504 plans on the tiny instance) -- and a candidate equals its moves applied one after the other."""
+    inst = I.make_instance("tiny", 0)
+    o = oracle_mod.Oracle(inst)
+    base = o.init_plan()
+    tours, bps = base.to_lists()
+    n2 = set()
+    for t, b in _neighbourhood(tours, bps, inst.n_tours):
+        n2 |= _neighbourhood([list(x) for x in t], [list(x) for x in b], inst.n_tours)
+    p = oracle_mod.make_params(seed=1000, gate=0, k_moves=2)
+    seen = set()
+    for i in range(1 << 14):
+        cand, mv = o.candidate(p, 0, i, base)
+        if i < 200:
+            assert o.apply(o.apply(base, mv[0]), mv[1]) == cand
+        t, b = cand.to_lists()
+        seen.add((tuple(map(tuple, t)), tuple(map(tuple, b))))
+    assert seen == n2 and len(n2) == 504
+    # the batch scorer scores exactly these candidates
+    r = o.score_batch(p, 0, base, 256)
+    for i in range(256):
+        cand, mv = o.candidate(p, 0, i, base)
+        assert r["moves"][i].tolist() == mv.ravel().tolist()
+        s = o.score(cand, p)
+        assert (s["cost"] == r["cost"][i]) or (math.isinf(s["cost"]) and math.isinf(r["cost"][i]))
+
+
+def test_three_move_search_is_monotone_and_resumable(oracle_mod):
+    """With three chained moves per candidate the search keeps C* monotone and resumes exactly."""
+    inst = I.make_instance("paper", 2)
+    o = oracle_mod.Oracle(inst)
+    p = oracle_mod.make_params(seed=1000, gate=1, k_moves=3, eps=0.5)
+    a = o.start(p)
+    ra = o.search(p, a, 6, 2048, threads=4)
+    assert np.all(np.diff(ra["cstar"]) <= 0)
+    b = o.start(p)
+    o.search(p, b, 2, 2048, threads=4)
+    o.search(p, b, 4, 2048, threads=4)
+    assert b.xbest == a.xbest and b.xold == a.xold and b.cstar == a.cstar and b.iter == a.iter == 6
+
+
 def _all_plans(F, B, T):
     """Every plan of the tiny instance: BPs arranged over tours, fields arranged over BPs."""
     bp_arr = []

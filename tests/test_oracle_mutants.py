@@ -50,6 +50,10 @@ MUTANTS = {
     "margin_su_stop_new_scale": ("fmax(nm_scale, sscmx)", "nm_scale"),
     "margin_gate_dropped": ("note_gap(GAP_GATE, &margin, tmax, tmax_star, fmax(tmax, tmax_star));", "(void)0;"),
     "margin_keeps_largest": ("if (m < *margin) *margin = m;", "if (m > *margin || isinf(*margin)) *margin = m;"),
+    # chained moves (Step 8 repeated)
+    "second_move_drawn_on_base": ("draw_move(c, prm, iter, i, j, out, mv + 4 * j);",
+                                  "draw_move(c, prm, iter, i, j, base, mv + 4 * j);"),
+    "move_counter_word3_shared": ("return j == 0 ? 0u : (uint32_t)j + 1u;", "return (uint32_t)j;"),
     "margin_su_scale_max_of_terms": ("if (scale) *scale = fabs(drive) + fabs(fill);",
                                      "if (scale) *scale = fmax(fabs(drive), fabs(fill));"),
 }

@@ -56,6 +56,30 @@ def test_first_move_from_known_answer(oracle_mod):
     assert o.move(oracle_mod.make_params(seed=0, p_swap=0.6), 0, 0, x)[0] == 0
 
 
+def test_two_move_candidate_hand_trace(oracle_mod):
+    """Step 8 repeated (Sec. 2.5's second application), traced by hand on the tiny instance,
+    seed 0, candidate 0. Base: tours [[b0], [b1]], BP fields [[f0, f1], [f2, f4, f5, f3]].
+    Move 0, counter (0, 0, 0, 0) = the all-zero KAT input: v = floor(0x6627e8d5 * 8 / 2^32) = 3
+      (field 3, in b1 at position 3); BP = floor(0xe169c58d * 2 / 2^32) = 1; b1 has 3 fields
+      left, slot = floor(0xbc57ac4c * 4 / 2^32) = 2: b1 -> [f2, f4, f3, f5].
+    Move 1 is drawn on that plan from counter (0, 0, 0, 2) (word 3 = 1 is the eps rule's):
+      with its output words w0..w2, v = floor(w0 * 8 / 2^32) = 6, i.e. BP 0 (in tour 0);
+      tour = floor(w1 * 2 / 2^32) = 1; tour 1 holds 1 BP, slot = floor(w2 * 2 / 2^32) = 1:
+      tour 0 -> [], tour 1 -> [b1, b0]."""
+    inst = I.make_instance("tiny", 0)
+    o = oracle_mod.Oracle(inst)
+    base = o.init_plan()
+    assert base.to_lists() == ([[0], [1]], [[0, 1], [2, 4, 5, 3]])
+    w = [int(x) for x in oracle_mod.philox4x32_10([0, 0, 0, 2], [0, 0])]
+    assert (w[0] * 8) >> 32 == 6 and (w[1] * 2) >> 32 == 1 and (w[2] * 2) >> 32 == 1
+    cand, mv = o.candidate(oracle_mod.make_params(seed=0, k_moves=2), 0, 0, base)
+    assert mv.tolist() == [[0, 3, 1, 2], [1, 0, 1, 1]]
+    assert cand.to_lists() == ([[], [1, 0]], [[0, 1], [2, 4, 3, 5]])
+    # with one move the candidate stops after move 0
+    one, mv1 = o.candidate(oracle_mod.make_params(seed=0), 0, 0, base)
+    assert mv1.tolist() == [[0, 3, 1, 2]] and one.to_lists() == ([[0], [1]], [[0, 1], [2, 4, 3, 5]])
+
+
 def _fig1():
     """Fig. 1 as an instance: node positions read from the figure."""
     pos = {}
