@@ -99,6 +99,10 @@ typedef struct bl_params {
                                 of that many lanes of a warp scores it together, lane g holding
                                 tour g (>= the largest tour count; 4 or 8 for <= 4 tours, 8 or
                                 16 for <= 6, 16 or 32 above; else BL_EINVAL). Same results. */
+    int32_t k_moves;         /* 0 or 1: one remove-and-reinsert move per candidate (Step 8);
+                                2 or 3: Step 8 repeated, move j drawn on the plan the first j
+                                moves made (Philox counter word 3 = 0, then j + 1); needs
+                                lanes_per_cand <= 1 and no learned proposals (else BL_EINVAL) */
     void *workspace;         /* device, optional: caller-owned buffer of
                                 bl_workspace_bytes() bytes, 256-byte aligned; NULL = the
                                 library allocates and frees its own */
@@ -200,9 +204,11 @@ int bl_get_log(bl_handle *h, int32_t inst, uint32_t first, int32_t n, int32_t *i
    base x* (use_best = 1) or x_old (0) of instance `inst`, without updating
    anything; tmax_star is the gate's reference (pass the state's Tmax*).
    Host outputs (any may be NULL): cost[n], tmax[n] (FP32; +inf when
-   infeasible), moves[n x 4] ({kind, vertex, a, b}: kind 0 field reinsert
-   (a = BP, b = slot), 1 BP reinsert (a = tour, b = slot), 2 field swap
-   (a = other field), 3 BP swap (a = other BP)), n_hu[n x T], n_su[n x T],
+   infeasible), moves[n x 4 k] (k = params.k_moves records {kind, vertex,
+   a, b} per candidate, move j relative to the plan after the first j:
+   kind 0 field reinsert (a = BP, b = slot), 1 BP reinsert (a = tour, b =
+   slot), 2 field swap (a = other field), 3 BP swap (a = other BP)),
+   n_hu[n x T], n_su[n x T],
    and the HU and SU assignments the two local minimisations of Sec. 2.5
    reach, hu_tour[n x H] and su_tour[n x S] (tour of each unit by id, -1
    when unassigned: infeasible candidates). */

@@ -48,7 +48,8 @@ class bl_params(C.Structure):
     _fields_ = [("eps", C.c_float), ("p_swap", C.c_float), ("seed", C.c_uint64), ("inst_idx", C.c_uint32),
                 ("n_cand", C.c_int32), ("fix_field_bp", C.c_int32), ("fix_resources", C.c_int32),
                 ("gate", C.c_int32), ("block_threads", C.c_int32), ("blocks_per_sm", C.c_int32), ("tile", C.c_int32),
-                ("log_capacity", C.c_int32), ("lanes_per_cand", C.c_int32), ("workspace", C.c_void_p),
+                ("log_capacity", C.c_int32), ("lanes_per_cand", C.c_int32), ("k_moves", C.c_int32),
+                ("workspace", C.c_void_p),
                 ("workspace_bytes", C.c_size_t)]
 
 
@@ -129,10 +130,11 @@ class _InstanceArgs:
 
 def make_params(n_cand: int, eps: float = 0.5, seed: int = 0, inst_idx: int = 0, fix_field_bp: int = 0,
                 fix_resources: int = 0, gate: int = 1, p_swap: float = 0.0, block_threads: int = 0,
-                blocks_per_sm: int = 0, tile: int = 0, log_capacity: int = 0, lanes_per_cand: int = 0) -> bl_params:
+                blocks_per_sm: int = 0, tile: int = 0, log_capacity: int = 0, lanes_per_cand: int = 0,
+                k_moves: int = 1) -> bl_params:
     return bl_params(float(eps), float(p_swap), int(seed), int(inst_idx), int(n_cand), int(fix_field_bp),
                      int(fix_resources), int(gate), int(block_threads), int(blocks_per_sm), int(tile),
-                     int(log_capacity), int(lanes_per_cand), None, 0)
+                     int(log_capacity), int(lanes_per_cand), int(k_moves), None, 0)
 
 
 def _check(rc: int, handle=None):
@@ -230,7 +232,8 @@ class Search:
                          units: bool = False) -> dict:
         I = self.instances[inst]
         T = I.n_tours
-        o = dict(cost=np.zeros(n, np.float32), tmax=np.zeros(n, np.float32), moves=np.zeros((n, 4), np.int16),
+        km = max(1, int(self.params.k_moves))
+        o = dict(cost=np.zeros(n, np.float32), tmax=np.zeros(n, np.float32), moves=np.zeros((n, 4 * km), np.int16),
                  n_hu=np.zeros((n, T), np.int16), n_su=np.zeros((n, T), np.int16))
         if units:
             o.update(hu_tour=np.zeros((n, I.n_hu), np.int16), su_tour=np.zeros((n, I.n_su), np.int16))

@@ -530,6 +530,14 @@ int init_common(const bl_instance *insts, int32_t n_inst, const bl_params *param
         return BL_EINVAL;
     }
     if (params->gate < 0 || params->gate > 2) { g_error = "gate must be 0, 1 or 2"; return BL_EINVAL; }
+    if (params->k_moves < 0 || params->k_moves > kMaxMoves) {
+        g_error = "k_moves must be in [0, " + std::to_string(kMaxMoves) + "]";
+        return BL_EINVAL;
+    }
+    if (params->k_moves > 1 && params->lanes_per_cand > 1) {
+        g_error = "chained moves (k_moves > 1) are scored one thread per candidate: lanes_per_cand must be <= 1";
+        return BL_EINVAL;
+    }
     bl_handle *h = new bl_handle();
     h->n_inst = n_inst;
     h->prm = *params;
@@ -542,6 +550,7 @@ int init_common(const bl_instance *insts, int32_t n_inst, const bl_params *param
     h->sp.fix_field_bp = params->fix_field_bp;
     h->sp.fix_resources = params->fix_resources;
     h->sp.gate = params->gate;
+    h->sp.k_moves = params->k_moves <= 1 ? 1 : params->k_moves;
     h->insts.resize((size_t)n_inst);
     for (int i = 0; i < n_inst; ++i) {
         std::string err;
@@ -938,7 +947,8 @@ int bl_score_candidates(bl_handle *h, int32_t inst, int32_t use_best, uint32_t i
     const HostInst &hi = h->insts[(size_t)inst];
     const int T = hi.T, H = hi.H, S = hi.S;
     const size_t nh = hu_tour ? (size_t)H : 0, ns = su_tour ? (size_t)S : 0;
-    const size_t per = 4 + 4 + 8 + 4 * (size_t)T + 2 * (nh + ns) + 16;
+    const size_t km = (size_t)h->sp.k_moves;   // move records per candidate
+    const size_t per = 4 + 4 + 8 * km + 4 * (size_t)T + 2 * (nh + ns) + 16;
     const int chunk = (int)((kScratchBytes - 1024) / per);
     unsigned char *s = h->at<unsigned char>(h->ws.scratch);
     for (int k0 = 0; k0 < n; k0 += chunk) {
@@ -946,7 +956,7 @@ int bl_score_candidates(bl_handle *h, int32_t inst, int32_t use_best, uint32_t i
         float *dc = (float *)s;
         float *dt = dc + m;
         int16_t *dm = (int16_t *)(dt + m);
-        int16_t *dh = dm + 4 * (size_t)m;
+        int16_t *dh = dm + 4 * km * (size_t)m;
         int16_t *ds = dh + (size_t)m * T;
         int16_t *dhu = hu_tour ? ds + (size_t)m * T : nullptr;
         int16_t *dsu = su_tour ? ds + (size_t)m * T + (size_t)m * nh : nullptr;
@@ -954,7 +964,9 @@ int bl_score_candidates(bl_handle *h, int32_t inst, int32_t use_best, uint32_t i
                                 h->sp, dc, dt, dm, dh, ds, nullptr, nullptr, nullptr, dhu, dsu, h->stream));
         if (cost) CK(h, cudaMemcpyAsync(cost + k0, dc, 4 * (size_t)m, cudaMemcpyDeviceToHost, h->stream));
         if (tmax) CK(h, cudaMemcpyAsync(tmax + k0, dt, 4 * (size_t)m, cudaMemcpyDeviceToHost, h->stream));
-        if (moves) CK(h, cudaMemcpyAsync(moves + 4 * (size_t)k0, dm, 8 * (size_t)m, cudaMemcpyDeviceToHost, h->stream));
+        if (moves)
+            CK(h, cudaMemcpyAsync(moves + 4 * km * (size_t)k0, dm, 8 * km * (size_t)m, cudaMemcpyDeviceToHost,
+                                  h->stream));
         if (n_hu) CK(h, cudaMemcpyAsync(n_hu + (size_t)k0 * T, dh, 2 * (size_t)m * T, cudaMemcpyDeviceToHost, h->stream));
         if (n_su) CK(h, cudaMemcpyAsync(n_su + (size_t)k0 * T, ds, 2 * (size_t)m * T, cudaMemcpyDeviceToHost, h->stream));
         if (hu_tour)
@@ -998,6 +1010,7 @@ int bl_argmin_noalloc(bl_handle *h, int32_t inst, int32_t use_best, uint32_t ite
     }
     if (!h || inst < 0 || inst >= h->n_inst || !d_key || !d_tmax) return BL_EINVAL;
     if (h->failed) return BL_ESTATE;
+    if (h->sp.k_moves > 1) { h->err = "bl_argmin_noalloc scores one-move candidates only"; return BL_EINVAL; }
     int dev = -1;
     CK(h, cudaGetDevice(&dev));
     if (dev != h->dev) {
@@ -1015,6 +1028,7 @@ int bl_features(bl_handle *h, int32_t inst, int32_t use_best, uint32_t iter, int
 {
     if (!h || inst < 0 || inst >= h->n_inst || i0 < 0 || n < 1 || !d_feat) return BL_EINVAL;
     if (h->failed) return BL_ESTATE;
+    if (h->sp.k_moves > 1) { h->err = "bl_features describes one-move candidates only"; return BL_EINVAL; }
     CK(h, launch_features(h->cfg, h->at<InstMeta>(h->ws.meta), inst, use_best, iter, i0, n, h->sp, d_feat, d_base_cost,
                           h->stream));
     return BL_OK;
@@ -1025,6 +1039,7 @@ int bl_search_step_learned(bl_handle *h, bl_mlp *mlp, int32_t n_iters, int32_t p
     if (!h || !mlp || n_iters < 0 || pool < 1 || n_keep < 1 || n_keep > pool || !(rand_frac >= 0.f && rand_frac <= 1.f))
         return BL_EINVAL;
     if (h->failed) return BL_ESTATE;
+    if (h->sp.k_moves > 1) { h->err = "learned proposals rank one-move candidates only"; return BL_EINVAL; }
     if (mlp_stream_of(mlp) != h->stream) {
         h->err = "learned proposals: create the MLP on the search handle's stream";
         return BL_EINVAL;

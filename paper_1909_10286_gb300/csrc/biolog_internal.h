@@ -88,7 +88,9 @@ struct SearchParams {
     int32_t fix_field_bp;
     int32_t fix_resources;
     int32_t gate;
+    int32_t k_moves;           // moves chained per candidate (Step 8 repeated), 1..kMaxMoves
 };
+constexpr int kMaxMoves = 3;
 
 // One work item: a contiguous candidate range of one instance.
 struct WorkItem {

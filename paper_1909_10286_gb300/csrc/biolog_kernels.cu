@@ -324,6 +324,183 @@ struct View {
     }
 };
 
+// ---------------------------------------------------------------------------
+// Candidates of k chained moves (Step 8 repeated; Sec. 2.5 mentions applying
+// it a second time): level l turns the plan after l moves (plan l) into plan
+// l + 1, and queries descend the levels by index remapping down to the base
+// plan -- nothing is materialised. Move j is drawn on plan j from Philox
+// counter (i, iter, inst, 0) for j = 0 and (i, iter, inst, j + 1) after
+// (word 3 = 1 is the eps rule's counter).
+// ---------------------------------------------------------------------------
+struct Lvl {
+    int kind;   // 0 field reinsert, 1 BP reinsert, 2 field swap, 3 BP swap
+    int v, w;   // moved vertex; swap partner
+    int s, sp;  // reinserts: source group (BP or tour) and position in plan l
+    int d, dp;  // destination group and slot in its list after the removal
+};
+
+__device__ __forceinline__ int swap_id(int q, int v, int w) { return q == v ? w : (q == w ? v : q); }
+
+struct ChainView {
+    int n;   // levels (moves)
+    Lvl L[kMaxMoves];
+
+    // length of tour g / BP b in plan m
+    __device__ __forceinline__ int tour_len(const Ctx &c, int g, int m) const
+    {
+        int len = c.tour_cnt[g];
+#pragma unroll
+        for (int l = 0; l < kMaxMoves; ++l)
+            if (l < m && L[l].kind == 1) len += (g == L[l].d ? 1 : 0) - (g == L[l].s ? 1 : 0);
+        return len;
+    }
+    __device__ __forceinline__ int bp_len(const Ctx &c, int b, int m) const
+    {
+        int len = c.bp_cnt[b];
+#pragma unroll
+        for (int l = 0; l < kMaxMoves; ++l)
+            if (l < m && L[l].kind == 0) len += (b == L[l].d ? 1 : 0) - (b == L[l].s ? 1 : 0);
+        return len;
+    }
+    // BP at position j of tour g in plan m: undo the levels' insertions and removals down to the
+    // base, then redo the swaps of the levels above the one that placed it
+    __device__ __forceinline__ int bp_at(const Ctx &c, int g, int j, int m) const
+    {
+        int res = -1, up = 0;
+#pragma unroll
+        for (int l = kMaxMoves - 1; l >= 0; --l) {
+            if (l >= m || res >= 0 || L[l].kind != 1) continue;
+            if (g == L[l].d) {
+                if (j == L[l].dp) { res = L[l].v; up = l + 1; continue; }
+                j -= (j > L[l].dp ? 1 : 0);
+            }
+            if (g == L[l].s) j += (j >= L[l].sp ? 1 : 0);
+        }
+        if (res < 0) res = c.bp_order[c.tour_start[g] + j];
+#pragma unroll
+        for (int l = 0; l < kMaxMoves; ++l)
+            if (l >= up && l < m && L[l].kind == 3) res = swap_id(res, L[l].v, L[l].w);
+        return res;
+    }
+    // field at position k of BP b in plan m
+    __device__ __forceinline__ int field_at(const Ctx &c, int b, int k, int m) const
+    {
+        int res = -1, up = 0;
+#pragma unroll
+        for (int l = kMaxMoves - 1; l >= 0; --l) {
+            if (l >= m || res >= 0 || L[l].kind != 0) continue;
+            if (b == L[l].d) {
+                if (k == L[l].dp) { res = L[l].v; up = l + 1; continue; }
+                k -= (k > L[l].dp ? 1 : 0);
+            }
+            if (b == L[l].s) k += (k >= L[l].sp ? 1 : 0);
+        }
+        if (res < 0) res = c.field_order[c.bp_start[b] + k];
+#pragma unroll
+        for (int l = 0; l < kMaxMoves; ++l)
+            if (l >= up && l < m && L[l].kind == 2) res = swap_id(res, L[l].v, L[l].w);
+        return res;
+    }
+    // tour and position of BP b in plan m: follow its slot down through the swaps to the level
+    // that inserted it (or the base), then shift the position by the reinserts above
+    __device__ __forceinline__ void bp_place(const Ctx &c, int b, int m, int &t, int &p) const
+    {
+        int q = b, stop = -1;
+#pragma unroll
+        for (int l = kMaxMoves - 1; l >= 0; --l) {
+            if (l >= m || stop >= 0) continue;
+            if (L[l].kind == 1 && q == L[l].v) { stop = l; continue; }
+            if (L[l].kind == 3) q = swap_id(q, L[l].v, L[l].w);
+        }
+        if (stop >= 0) { t = L[stop].d; p = L[stop].dp; }
+        else { t = c.bp_tour[q]; p = c.bp_pos[q]; }
+#pragma unroll
+        for (int l = 0; l < kMaxMoves; ++l)
+            if (l > stop && l < m && L[l].kind == 1) {
+                p -= (t == L[l].s && p > L[l].sp) ? 1 : 0;
+                p += (t == L[l].d && p >= L[l].dp) ? 1 : 0;
+            }
+    }
+    // BP and position of field f in plan m
+    __device__ __forceinline__ void field_place(const Ctx &c, int f, int m, int &b, int &p) const
+    {
+        int q = f, stop = -1;
+#pragma unroll
+        for (int l = kMaxMoves - 1; l >= 0; --l) {
+            if (l >= m || stop >= 0) continue;
+            if (L[l].kind == 0 && q == L[l].v) { stop = l; continue; }
+            if (L[l].kind == 2) q = swap_id(q, L[l].v, L[l].w);
+        }
+        if (stop >= 0) { b = L[stop].d; p = L[stop].dp; }
+        else { b = c.field_bp[q]; p = c.field_pos[q]; }
+#pragma unroll
+        for (int l = 0; l < kMaxMoves; ++l)
+            if (l > stop && l < m && L[l].kind == 0) {
+                p -= (b == L[l].s && p > L[l].sp) ? 1 : 0;
+                p += (b == L[l].d && p >= L[l].dp) ? 1 : 0;
+            }
+    }
+    __device__ __forceinline__ int tour_of_bp(const Ctx &c, int b) const { int t, p; bp_place(c, b, n, t, p); return t; }
+    __device__ __forceinline__ int bp_of_field(const Ctx &c, int f) const { int b, p; field_place(c, f, n, b, p); return b; }
+    // tours whose content may differ from the base plan: every tour some level changed, in the
+    // BP-to-tour mapping of that level's plan (a superset)
+    __device__ __forceinline__ unsigned touched(const Ctx &c) const
+    {
+        unsigned t = 0u;
+#pragma unroll
+        for (int l = 0; l < kMaxMoves; ++l) {
+            if (l >= n) continue;
+            const Lvl &e = L[l];
+            int g0, g1, p, b0, b1;
+            switch (e.kind) {
+            case 0: bp_place(c, e.s, l, g0, p); bp_place(c, e.d, l, g1, p); break;
+            case 1: g0 = e.s; g1 = e.d; break;
+            case 2:
+                field_place(c, e.v, l, b0, p); field_place(c, e.w, l, b1, p);
+                bp_place(c, b0, l, g0, p); bp_place(c, b1, l, g1, p);
+                break;
+            default: bp_place(c, e.v, l, g0, p); bp_place(c, e.w, l, g1, p);
+            }
+            t |= (1u << g0) | (1u << g1);
+        }
+        return t;
+    }
+};
+
+// Step 8 applied k times: move j drawn on plan j with the same rules as draw_move.
+__device__ __forceinline__ void draw_chain(const Ctx &c, const SearchParams &p, uint32_t i, uint32_t iter,
+                                           uint32_t inst_idx, ChainView &cv)
+{
+    cv.n = 0;
+#pragma unroll
+    for (int j = 0; j < kMaxMoves; ++j) {
+        if (j >= p.k_moves) continue;
+        uint32_t r[4] = {i, iter, inst_idx, j == 0 ? 0u : (uint32_t)j + 1u};
+        philox10(r, p.seed_lo, p.seed_hi);
+        const int v = (int)__umulhi(r[0], (uint32_t)(c.F + c.B));
+        Lvl e = {4, 0, 0, -1, -1, -1, -1};
+        if (unit24f(r[3]) < p.p_swap) {
+            if (v < c.F) { e.kind = 2; e.v = v; e.w = (int)__umulhi(r[1], (uint32_t)c.F); }
+            else { e.kind = 3; e.v = v - c.F; e.w = (int)__umulhi(r[1], (uint32_t)c.B); }
+        } else if (v < c.F) {
+            int bs, ps;
+            cv.field_place(c, v, j, bs, ps);
+            const int bd = p.fix_field_bp ? bs : (int)__umulhi(r[1], (uint32_t)c.B);
+            const int len = cv.bp_len(c, bd, j) - (bd == bs ? 1 : 0);
+            e = {0, v, 0, bs, ps, bd, (int)__umulhi(r[2], (uint32_t)(len + 1))};
+        } else {
+            const int b = v - c.F;
+            int gs, ps;
+            cv.bp_place(c, b, j, gs, ps);
+            const int gd = (int)__umulhi(r[1], (uint32_t)c.T);
+            const int len = cv.tour_len(c, gd, j) - (gd == gs ? 1 : 0);
+            e = {1, b, 0, gs, ps, gd, (int)__umulhi(r[2], (uint32_t)(len + 1))};
+        }
+        cv.L[j] = e;
+        cv.n = j + 1;
+    }
+}
+
 // Route aggregates (Fig. 1, Sec. 2.2), exact in fixed point so that they do
 // not depend on summation order: every per-tour value is a function of the
 // tour's content only.
@@ -470,6 +647,82 @@ __device__ __forceinline__ bool demand_ok(const Ctx &c, const MoveRec &m)
     return c.nbad == 0;
 }
 
+// The same aggregates for a candidate of chained moves, walked through the chain's view.
+__device__ __forceinline__ BpAgg walk_bp_chain(const Ctx &c, const ChainView &cv, int b)
+{
+    BpAgg r;
+    r.nf = cv.bp_len(c, b, cv.n);
+    r.internal = r.sb = r.area = 0;
+    r.first = r.last = -1;
+    const int bn = 1 + b;
+    int prev = -1;
+    for (int k = 0; k < r.nf; ++k) {
+        const int fn = 1 + c.B + cv.field_at(c, b, k, cv.n);
+        if (prev >= 0) r.internal += c.dq(prev, fn);
+        else r.first = fn;
+        r.sb += c.dq(fn, bn);
+        r.area += c.areaq[fn - 1 - c.B];
+        prev = fn;
+    }
+    r.last = prev;
+    return r;
+}
+
+__device__ __forceinline__ TourAgg tour_agg_chain(const Ctx &c, const ChainView &cv, int g, int nb)
+{
+    TourAgg t;
+    t.LHU = t.LSU = t.A = 0;
+    int prev_last = 0, anchor = 0, nonempty = 0;
+    float dsum = 0.f;
+    for (int j = 0; j < nb; ++j) {
+        const int b = cv.bp_at(c, g, j, cv.n);
+        const BpAgg a = walk_bp_chain(c, cv, b);
+        if (a.nf == 0) continue;   // BPs without fields are skipped in routing
+        t.LHU += c.dq(prev_last, a.first) + a.internal;
+        t.LSU += c.dq(anchor, a.first);
+        t.A += a.area;
+        dsum = __fadd_rn(dsum, __fmul_rn(__fmul_rn(__ll2float_rn(a.sb), c.dq_scale), c.rcp[a.nf]));
+        prev_last = a.last;
+        anchor = 1 + b;
+        ++nonempty;
+    }
+    t.LHU += c.dq(prev_last, 0);
+    t.LSU += c.dq(anchor, 0);
+    t.DB2 = nonempty ? __fmul_rn(2.0f, __fmul_rn(dsum, c.rcp[nonempty])) : 0.f;
+    return t;
+}
+
+// Eq. 2 for a candidate of chained moves: the BPs some field move touched are re-summed exactly
+// over their fields in the final plan; the others keep the base's status.
+__device__ __forceinline__ bool demand_ok_chain(const Ctx &c, const ChainView &cv)
+{
+    int bl[2 * kMaxMoves];
+    int nb = 0;
+#pragma unroll
+    for (int l = 0; l < kMaxMoves; ++l) {
+        if (l >= cv.n) continue;
+        const Lvl &e = cv.L[l];
+        int b0 = -1, b1 = -1, p;
+        if (e.kind == 0) { b0 = e.s; b1 = e.d; }
+        else if (e.kind == 2) { cv.field_place(c, e.v, l, b0, p); cv.field_place(c, e.w, l, b1, p); }
+        if (b0 >= 0 && b0 != b1) { bl[nb++] = b0; bl[nb++] = b1; }
+    }
+    int others = c.nbad;
+    bool ok = true;
+    for (int q = 0; q < nb; ++q) {
+        const int b = bl[q];
+        bool dup = false;
+        for (int r = 0; r < q; ++r) dup |= (bl[r] == b);
+        if (dup) continue;
+        others -= c.bad[b];
+        long long sum = 0;
+        const int nf = cv.bp_len(c, b, cv.n);
+        for (int k = 0; k < nf; ++k) sum += c.supq[cv.field_at(c, b, k, cv.n)];
+        ok &= sum >= c.demq[b];
+    }
+    return ok && others == 0;
+}
+
 // Eq. 4: n = ceil(s * nsu / cap). FP32 fast path; within 2^-21 of an integer the
 // smallest k with k * cap >= s * nsu is found exactly in FP64 (a - p is exact
 // by Sterbenz since p is within 1e-6 of a; k*cap = p + e exactly by FMA).
@@ -572,11 +825,14 @@ struct TourState {
 // is +inf if the gate discards the candidate, else 0 (not a cost); Tmax depends
 // on the HU assignment alone, so the gate decision is final at that point.
 // STAGE 2: the rest of the score, resumed from a Survivor record of stage 1.
-template <class SH, bool DUMP, bool IDENT = false, int STAGE = 0>
+// CHAIN: the candidate is the chained moves of *cv (m is ignored); its route aggregates and
+// shuttle sums are walked through the chain's view.
+template <class SH, bool DUMP, bool IDENT = false, int STAGE = 0, bool CHAIN = false>
 __device__ ScoreOut score_candidate(const Ctx &c, const SearchParams &p, const MoveRec &m, float tmax_star,
                                     unsigned char *tstate, int tid, int16_t *o_nhu, int16_t *o_nsu, float *o_tc,
                                     float *o_tw, float *o_tcost, int16_t *o_hu, int16_t *o_su, float *o_kf = nullptr,
-                                    long long *o_sh = nullptr, const Survivor<SH> *rec = nullptr)
+                                    long long *o_sh = nullptr, const Survivor<SH> *rec = nullptr,
+                                    const ChainView *cv = nullptr)
 {
     constexpr int MAXT = SH::MAXT, SW = SH::SW;
     using M = typename SH::Mask;
@@ -593,7 +849,8 @@ __device__ ScoreOut score_candidate(const Ctx &c, const SearchParams &p, const M
 #define FOR_ACTIVE(g) _Pragma("unroll") for (int g = 0; g < MAXT; ++g) if ((amask >> g) & 1u)
     ScoreOut out;
     View x;
-    x.set(c, m);
+    if constexpr (CHAIN) x.set(c, MoveRec{4, 0, 0, 0});
+    else x.set(c, m);
 
     if constexpr (STAGE == 2) {
         amask = rec->amask;
@@ -607,16 +864,22 @@ __device__ ScoreOut score_candidate(const Ctx &c, const SearchParams &p, const M
             }
     } else {
     // --- route aggregates (Fig. 1, Sec. 2.2): rebuild the touched tours, reuse the base's
-    const unsigned touched = x.touched(c);
+    unsigned touched;
+    if constexpr (CHAIN) touched = cv->touched(c);
+    else touched = x.touched(c);
     for (int g = 0; g < c.T; ++g) {
-        const int nb = x.tour_len(c, g);
+        int nb;
+        if constexpr (CHAIN) nb = cv->tour_len(c, g, cv->n);
+        else nb = x.tour_len(c, g);
         if (nb == 0) continue;
         amask |= 1u << g;
         ++na;
         long long lhu, lsu, ar;
         float db2;
         if ((touched >> g) & 1u) {
-            const TourAgg t = tour_agg(c, x, g, nb);
+            TourAgg t;
+            if constexpr (CHAIN) t = tour_agg_chain(c, *cv, g, nb);
+            else t = tour_agg(c, x, g, nb);
             lhu = t.LHU; lsu = t.LSU; ar = t.A; db2 = t.DB2;
         } else {
             lhu = c.tLHU[g]; lsu = c.tLSU[g]; ar = c.tA[g]; db2 = c.tDB2[g];
@@ -822,8 +1085,9 @@ __device__ ScoreOut score_candidate(const Ctx &c, const SearchParams &p, const M
     // ratio N_SU/sum cap: if neither changed against the base plan, reuse the base's.
     unsigned fresh = amask;
     if (c.memo) {
-        unsigned moved = 0u;   // tours whose field -> BP content changed
-        if (x.kind == 0 && x.sg != x.dg) moved = (1u << c.bp_tour[x.sg]) | (1u << c.bp_tour[x.dg]);
+        unsigned moved = 0u;   // tours whose field -> BP content changed (chains: every touched tour)
+        if constexpr (CHAIN) moved = cv->touched(c);
+        else if (x.kind == 0 && x.sg != x.dg) moved = (1u << c.bp_tour[x.sg]) | (1u << c.bp_tour[x.dg]);
         else if (x.kind == 1 && x.sg != x.dg) moved = (1u << x.sg) | (1u << x.dg);
         else if (x.kind == 2 && c.field_bp[x.v] != c.field_bp[x.w])
             moved = (1u << c.bp_tour[c.field_bp[x.v]]) | (1u << c.bp_tour[c.field_bp[x.w]]);
@@ -851,7 +1115,27 @@ __device__ ScoreOut score_candidate(const Ctx &c, const SearchParams &p, const M
         if constexpr (IDENT) o_sh[g] = v0;
         shq += v0;
     }
-    if (fresh) {
+    if (CHAIN && fresh) {
+        // chained moves: walk the fresh tours' BPs through the chain's view
+        for (int b = 0; b < c.B; ++b) {
+            const int g = cv->tour_of_bp(c, b);
+            if (!((fresh >> g) & 1u)) continue;
+            float kf = kfv[0];
+#pragma unroll
+            for (int t = 1; t < MAXT; ++t)
+                if (g == t) kf = kfv[t];
+            long long acc = 0;
+            const int nf = cv->bp_len(c, b, cv->n);
+            for (int k = 0; k < nf; ++k) {
+                const int f = cv->field_at(c, b, k, cv->n);
+                const int n = ceil_n(g, c.supply[f], kf);
+                acc += (long long)n * c.dq(1 + c.B + f, 1 + b);
+            }
+            shq += acc;
+            if constexpr (DUMP) dSh[g] += acc;
+            if constexpr (IDENT) o_sh[g] += acc;
+        }
+    } else if (fresh) {
         // base positions of the fields that left their BP (added at their new BP below)
         int skip0 = -1, skip1 = -1;
         if (x.kind == 0 && x.sg != x.dg) skip0 = c.bp_start[x.sg] + c.field_pos[x.v];
@@ -1213,6 +1497,23 @@ __device__ void write_plan(const Ctx &c, const MoveRec &m, int16_t *out)
     for (int b = 0; b < c.B; ++b) out[c.B + c.T + c.F + b] = (int16_t)x.bp_len(c, b);
 }
 
+// Write a candidate of chained moves as an encoding.
+__device__ void write_plan_chain(const Ctx &c, const ChainView &cv, int16_t *out)
+{
+    int k = 0;
+    for (int g = 0; g < c.T; ++g) {
+        const int nb = cv.tour_len(c, g, cv.n);
+        for (int j = 0; j < nb; ++j) out[k++] = (int16_t)cv.bp_at(c, g, j, cv.n);
+    }
+    for (int g = 0; g < c.T; ++g) out[c.B + g] = (int16_t)cv.tour_len(c, g, cv.n);
+    k = c.B + c.T;
+    for (int b = 0; b < c.B; ++b) {
+        const int nf = cv.bp_len(c, b, cv.n);
+        for (int j = 0; j < nf; ++j) out[k++] = (int16_t)cv.field_at(c, b, j, cv.n);
+    }
+    for (int b = 0; b < c.B; ++b) out[c.B + c.T + c.F + b] = (int16_t)cv.bp_len(c, b, cv.n);
+}
+
 // ---------------------------------------------------------------------------
 // The search iteration kernel
 // ---------------------------------------------------------------------------
@@ -1220,7 +1521,7 @@ __device__ void write_plan(const Ctx &c, const MoveRec &m, int16_t *out)
 // warps) into its slot; the last work item of the instance to finish takes the
 // argmin over the instance's slots and runs Steps 13-16 (replay the move,
 // update x_old, x*, C*, Tmax*, the log and the iteration counter).
-template <int NT>
+template <int NT, bool CHAIN = false>
 __device__ __forceinline__ void block_argmin_finalize(unsigned long long best, float best_t, BlockShared &bs,
                                                       const InstMeta &M, const WorkItem &wi,
                                                       unsigned long long *__restrict__ slot_key,
@@ -1279,13 +1580,22 @@ __device__ __forceinline__ void block_argmin_finalize(unsigned long long best, f
                 InstState *st = M.state;
                 int ind = 0;
                 if (isfinite(cst)) {
-                    const MoveRec m = draw_move(c, prm, istar, iter, M.inst_idx);
-                    write_plan(c, m, M.xold);
+                    int kind0;
+                    if constexpr (CHAIN) {
+                        ChainView cv;
+                        draw_chain(c, prm, istar, iter, M.inst_idx, cv);
+                        write_plan_chain(c, cv, M.xold);
+                        kind0 = cv.L[0].kind;
+                    } else {
+                        const MoveRec m = draw_move(c, prm, istar, iter, M.inst_idx);
+                        write_plan(c, m, M.xold);
+                        kind0 = m.kind;
+                    }
                     if (cst < st->cstar) {
                         for (int k = 0; k < M.plan_len; ++k) M.xbest[k] = M.xold[k];
                         st->cstar = cst;
                         st->tmaxstar = bt;
-                        ind = (m.kind == 0 || m.kind == 2) ? 1 : 2;
+                        ind = (kind0 == 0 || kind0 == 2) ? 1 : 2;   // the (first) move's type (Fig. 3)
                     }
                 } else {
                     const int16_t *pl = c.bp_order;
@@ -1305,7 +1615,7 @@ __device__ __forceinline__ void block_argmin_finalize(unsigned long long best, f
     __syncthreads();
 }
 
-template <class SH>
+template <class SH, bool CHAIN>
 __global__ void __launch_bounds__(SH::NT, SH::MINB) search_iteration_kernel(const InstMeta *__restrict__ meta,
                                                                   const WorkItem *__restrict__ work, int32_t n_work,
                                                                   SearchParams prm, SmemPlan sp,
@@ -1397,8 +1707,14 @@ __global__ void __launch_bounds__(SH::NT, SH::MINB) search_iteration_kernel(cons
                 bool feas = false;
                 MoveRec m = {4, 0, 0, 0};
                 if (pos < c1) {
-                    m = draw_move(c, prm, (uint32_t)i, iter, M.inst_idx);
-                    feas = demand_ok(c, m);
+                    if constexpr (CHAIN) {   // the queue keeps i only: later stages draw the chain again
+                        ChainView cv;
+                        draw_chain(c, prm, (uint32_t)i, iter, M.inst_idx, cv);
+                        feas = demand_ok_chain(c, cv);
+                    } else {
+                        m = draw_move(c, prm, (uint32_t)i, iter, M.inst_idx);
+                        feas = demand_ok(c, m);
+                    }
                     if (!feas) {
                         const unsigned long long k = make_key(__int_as_float(0x7f800000), (uint32_t)i);
                         if (k < best) { best = k; best_t = __int_as_float(0x7f800000); }
@@ -1430,8 +1746,16 @@ __global__ void __launch_bounds__(SH::NT, SH::MINB) search_iteration_kernel(cons
                     i = qidx[slot];
                     pm = qmv[slot];
                     const MoveRec m = {pm.x & 0xffff, pm.x >> 16, pm.y & 0xffff, pm.y >> 16};
-                    r1 = score_candidate<SH, false, false, 1>(c, prm, m, tmax_star, tstate, tid, nullptr, nullptr, nullptr,
-                                                              nullptr, nullptr, nullptr, nullptr);
+                    if constexpr (CHAIN) {
+                        ChainView cv;
+                        draw_chain(c, prm, (uint32_t)i, iter, M.inst_idx, cv);
+                        r1 = score_candidate<SH, false, false, 1, true>(c, prm, m, tmax_star, tstate, tid, nullptr,
+                                                                        nullptr, nullptr, nullptr, nullptr, nullptr,
+                                                                        nullptr, nullptr, nullptr, nullptr, &cv);
+                    } else {
+                        r1 = score_candidate<SH, false, false, 1>(c, prm, m, tmax_star, tstate, tid, nullptr, nullptr,
+                                                                  nullptr, nullptr, nullptr, nullptr, nullptr);
+                    }
                     if (isinf(r1.cost)) {   // discarded by the gate: C = +inf (Sec. 2.5)
                         const unsigned long long k = make_key(r1.cost, (uint32_t)i);
                         if (k < best) { best = k; best_t = r1.tmax; }
@@ -1475,13 +1799,16 @@ __global__ void __launch_bounds__(SH::NT, SH::MINB) search_iteration_kernel(cons
                     const int2 pm = qmv2[slot];
                     const MoveRec m = {pm.x & 0xffff, pm.x >> 16, pm.y & 0xffff, pm.y >> 16};
                     ScoreOut r;
+                    ChainView cv;
+                    if constexpr (CHAIN) draw_chain(c, prm, (uint32_t)i, iter, M.inst_idx, cv);
                     if constexpr (kKeepSurvivors<SH>)
-                        r = score_candidate<SH, false, false, 2>(c, prm, m, tmax_star, tstate, tid, nullptr, nullptr,
-                                                                 nullptr, nullptr, nullptr, nullptr, nullptr, nullptr,
-                                                                 nullptr, &surv[slot]);
+                        r = score_candidate<SH, false, false, 2, CHAIN>(c, prm, m, tmax_star, tstate, tid, nullptr,
+                                                                        nullptr, nullptr, nullptr, nullptr, nullptr,
+                                                                        nullptr, nullptr, nullptr, &surv[slot], &cv);
                     else
-                        r = score_candidate<SH, false>(c, prm, m, tmax_star, tstate, tid, nullptr, nullptr, nullptr,
-                                                       nullptr, nullptr, nullptr, nullptr);
+                        r = score_candidate<SH, false, false, 0, CHAIN>(c, prm, m, tmax_star, tstate, tid, nullptr,
+                                                                        nullptr, nullptr, nullptr, nullptr, nullptr,
+                                                                        nullptr, nullptr, nullptr, nullptr, &cv);
                     const unsigned long long k = make_key(r.cost, (uint32_t)i);
                     if (k < best) { best = k; best_t = r.tmax; }
                     if (ins) ins[i] = make_float2(r.cost, r.tmax);
@@ -1496,7 +1823,7 @@ __global__ void __launch_bounds__(SH::NT, SH::MINB) search_iteration_kernel(cons
             }
             base = next;
         }
-        block_argmin_finalize<NT>(best, best_t, bs, M, wi, slot_key, slot_tmax, slot_base, c, prm, iter);
+        block_argmin_finalize<NT, CHAIN>(best, best_t, bs, M, wi, slot_key, slot_tmax, slot_base, c, prm, iter);
     }
 }
 
@@ -2023,7 +2350,7 @@ __global__ void __launch_bounds__(COOP_NT) search_iteration_coop_kernel(
 // ---------------------------------------------------------------------------
 // Inspection kernels
 // ---------------------------------------------------------------------------
-template <class SH>
+template <class SH, bool CHAIN>
 __global__ void __launch_bounds__(SH::NT) score_dump_kernel(const InstMeta *__restrict__ meta, int32_t inst,
                                                             int32_t use_best, uint32_t iter, float tmax_star,
                                                             int32_t i0, int32_t n, int32_t identity, SearchParams prm,
@@ -2047,10 +2374,25 @@ __global__ void __launch_bounds__(SH::NT) score_dump_kernel(const InstMeta *__re
     const int T = M.T;
     for (int k = blockIdx.x * nt + tid; k < n; k += gridDim.x * nt) {
         const int i = i0 + k;
-        MoveRec m = identity ? MoveRec{4, 0, 0, 0} : draw_move(c, prm, (uint32_t)i, bs.iter, M.inst_idx);
-        if (moves) {
-            moves[k * 4] = (int16_t)m.kind; moves[k * 4 + 1] = (int16_t)m.v;
-            moves[k * 4 + 2] = (int16_t)m.a; moves[k * 4 + 3] = (int16_t)m.b;
+        MoveRec m = {4, 0, 0, 0};
+        ChainView cv;
+        if constexpr (CHAIN) {
+            if (identity) cv.n = 0;   // the base plan itself: a chain of no moves
+            else draw_chain(c, prm, (uint32_t)i, bs.iter, M.inst_idx, cv);
+            // one record per move: {kind, vertex, BP / tour / partner, slot (0 for swaps)}
+            if (moves)
+                for (int l = 0; l < cv.n; ++l) {
+                    const Lvl &e = cv.L[l];
+                    int16_t *mv = moves + (size_t)k * 4 * prm.k_moves + 4 * l;
+                    mv[0] = (int16_t)e.kind; mv[1] = (int16_t)e.v;
+                    mv[2] = (int16_t)(e.kind < 2 ? e.d : e.w); mv[3] = (int16_t)(e.kind < 2 ? e.dp : 0);
+                }
+        } else {
+            if (!identity) m = draw_move(c, prm, (uint32_t)i, bs.iter, M.inst_idx);
+            if (moves) {
+                moves[k * 4] = (int16_t)m.kind; moves[k * 4 + 1] = (int16_t)m.v;
+                moves[k * 4 + 2] = (int16_t)m.a; moves[k * 4 + 3] = (int16_t)m.b;
+            }
         }
         int16_t *o_nhu = nhu ? nhu + (size_t)k * T : nullptr;
         int16_t *o_nsu = nsu ? nsu + (size_t)k * T : nullptr;
@@ -2069,16 +2411,19 @@ __global__ void __launch_bounds__(SH::NT) score_dump_kernel(const InstMeta *__re
         if (o_hu) for (int h = 0; h < M.H; ++h) o_hu[h] = -1;
         if (o_su) for (int s = 0; s < M.S; ++s) o_su[s] = -1;
         ScoreOut r;
-        if (demand_ok(c, m))
-            r = score_candidate<SH, true>(c, prm, m, tmax_star, tstate, tid, o_nhu, o_nsu, o_tc, o_tw, o_tk, o_hu,
-                                          o_su);
+        bool feas;
+        if constexpr (CHAIN) feas = demand_ok_chain(c, cv);
+        else feas = demand_ok(c, m);
+        if (feas)
+            r = score_candidate<SH, true, false, 0, CHAIN>(c, prm, m, tmax_star, tstate, tid, o_nhu, o_nsu, o_tc, o_tw,
+                                                           o_tk, o_hu, o_su, nullptr, nullptr, nullptr, &cv);
         else { r.cost = __int_as_float(0x7f800000); r.tmax = __int_as_float(0x7f800000); }
         if (cost) cost[k] = r.cost;
         if (tmax) tmax[k] = r.tmax;
     }
 }
 
-template <class SH>
+template <class SH, bool CHAIN>
 __global__ void __launch_bounds__(SH::NT) decode_kernel(const InstMeta *__restrict__ meta, int32_t inst,
                                                         int32_t use_best, uint32_t iter, const int32_t *idx, int32_t n,
                                                         SearchParams prm, SmemPlan sp, int16_t *plans)
@@ -2097,8 +2442,14 @@ __global__ void __launch_bounds__(SH::NT) decode_kernel(const InstMeta *__restri
     if (!stage_instance<SH>(M, bs, smem, sp, prm, use_best, iter, c)) return;
     const int rowlen = 2 * M.B + M.T + M.F;
     for (int k = blockIdx.x * nt + tid; k < n; k += gridDim.x * nt) {
-        const MoveRec m = draw_move(c, prm, (uint32_t)idx[k], bs.iter, M.inst_idx);
-        write_plan(c, m, plans + (size_t)k * rowlen);
+        if constexpr (CHAIN) {
+            ChainView cv;
+            draw_chain(c, prm, (uint32_t)idx[k], bs.iter, M.inst_idx, cv);
+            write_plan_chain(c, cv, plans + (size_t)k * rowlen);
+        } else {
+            const MoveRec m = draw_move(c, prm, (uint32_t)idx[k], bs.iter, M.inst_idx);
+            write_plan(c, m, plans + (size_t)k * rowlen);
+        }
     }
 }
 
@@ -2638,15 +2989,37 @@ size_t shared_bytes(int32_t shape, int32_t threads, int32_t max_prefix, int32_t 
     return plan_for(cfg).total;
 }
 
+// f(Shape{}, std::integral_constant<bool, chain>{}) for the shape class `shape`
+template <class F>
+static cudaError_t with_shape(int32_t shape, bool chain, F &&f)
+{
+    using T = std::true_type;
+    using N = std::false_type;
+    switch (shape) {
+    case SHAPE_T4_S64_DSMEM: return chain ? f(ShapeA{}, T{}) : f(ShapeA{}, N{});
+    case SHAPE_T6_S64_GMEM: return chain ? f(ShapeB{}, T{}) : f(ShapeB{}, N{});
+    case SHAPE_T10_S128_GMEM: return chain ? f(ShapeD{}, T{}) : f(ShapeD{}, N{});
+    default: return chain ? f(ShapeC{}, T{}) : f(ShapeC{}, N{});
+    }
+}
+
+template <class SH, bool CHAIN>
+static cudaError_t set_attrs_of(size_t smem)
+{
+    cudaError_t e = cudaFuncSetAttribute(search_iteration_kernel<SH, CHAIN>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(score_dump_kernel<SH, CHAIN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(decode_kernel<SH, CHAIN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+}
+
 template <class SH>
 static cudaError_t set_attrs(size_t smem)
 {
-    cudaError_t e =
-        cudaFuncSetAttribute(search_iteration_kernel<SH>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    const cudaError_t e = set_attrs_of<SH, false>(smem);
     if (e != cudaSuccess) return e;
-    e = cudaFuncSetAttribute(score_dump_kernel<SH>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    return cudaFuncSetAttribute(decode_kernel<SH>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    return set_attrs_of<SH, true>(smem);
 }
 
 cudaError_t configure_kernels(int32_t shape, size_t smem)
@@ -2668,16 +3041,16 @@ int search_blocks_per_sm(int32_t shape, size_t smem)
     cudaError_t e;
     switch (shape) {
     case SHAPE_T4_S64_DSMEM:
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, search_iteration_kernel<ShapeA>, ShapeA::NT, smem);
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, search_iteration_kernel<ShapeA, false>, ShapeA::NT, smem);
         break;
     case SHAPE_T6_S64_GMEM:
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, search_iteration_kernel<ShapeB>, ShapeB::NT, smem);
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, search_iteration_kernel<ShapeB, false>, ShapeB::NT, smem);
         break;
     case SHAPE_T10_S128_GMEM:
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, search_iteration_kernel<ShapeD>, ShapeD::NT, smem);
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, search_iteration_kernel<ShapeD, false>, ShapeD::NT, smem);
         break;
     default:
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, search_iteration_kernel<ShapeC>, ShapeC::NT, smem);
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, search_iteration_kernel<ShapeC, false>, ShapeC::NT, smem);
     }
     return e == cudaSuccess ? n : 0;
 }
@@ -2698,27 +3071,14 @@ cudaError_t launch_search_iteration(const LaunchCfg &cfg, const InstMeta *d_meta
         return cudaGetLastError();
     }
     const SmemPlan sp = plan_for(cfg);
-    switch (cfg.shape) {
-    case SHAPE_T4_S64_DSMEM:
-        search_iteration_kernel<ShapeA><<<cfg.grid, ShapeA::NT, sp.total, s>>>(
+    const cudaError_t e = with_shape(cfg.shape, prm.k_moves > 1, [&](auto sh, auto ch) {
+        using SH = decltype(sh);
+        search_iteration_kernel<SH, decltype(ch)::value><<<cfg.grid, SH::NT, sp.total, s>>>(
             d_meta, d_work, n_work, prm, sp, slot_key, slot_tmax, slot_base, cand_list, cand_count, list_stride, insp,
             insp_stride);
-        break;
-    case SHAPE_T6_S64_GMEM:
-        search_iteration_kernel<ShapeB><<<cfg.grid, ShapeB::NT, sp.total, s>>>(
-            d_meta, d_work, n_work, prm, sp, slot_key, slot_tmax, slot_base, cand_list, cand_count, list_stride, insp,
-            insp_stride);
-        break;
-    case SHAPE_T10_S128_GMEM:
-        search_iteration_kernel<ShapeD><<<cfg.grid, ShapeD::NT, sp.total, s>>>(
-            d_meta, d_work, n_work, prm, sp, slot_key, slot_tmax, slot_base, cand_list, cand_count, list_stride, insp,
-            insp_stride);
-        break;
-    default:
-        search_iteration_kernel<ShapeC><<<cfg.grid, ShapeC::NT, sp.total, s>>>(
-            d_meta, d_work, n_work, prm, sp, slot_key, slot_tmax, slot_base, cand_list, cand_count, list_stride, insp,
-            insp_stride);
-    }
+        return cudaSuccess;
+    });
+    if (e != cudaSuccess) return e;
     return cudaGetLastError();
 }
 
@@ -2830,17 +3190,14 @@ cudaError_t launch_score_dump(const LaunchCfg &cfg, const InstMeta *d_meta, int3
     int grid = (n + nt - 1) / nt;
     if (grid > cfg.grid) grid = cfg.grid;
     if (grid < 1) grid = 1;
-#define DUMP_ARGS d_meta, inst, use_best, iter, tmax_star, i0, n, identity, prm, sp, d_cost, d_tmax, d_moves, d_nhu, \
-                  d_nsu, d_tcompl, d_twait, d_tcost, d_hu_tour, d_su_tour
-    switch (cfg.shape) {
-    case SHAPE_T4_S64_DSMEM: score_dump_kernel<ShapeA><<<grid, nt, sp.total, s>>>(DUMP_ARGS); break;
-    case SHAPE_T6_S64_GMEM: score_dump_kernel<ShapeB><<<grid, nt, sp.total, s>>>(DUMP_ARGS); break;
-    case SHAPE_T10_S128_GMEM:
-        score_dump_kernel<ShapeD><<<grid, nt, sp.total, s>>>(DUMP_ARGS);
-        break;
-    default: score_dump_kernel<ShapeC><<<grid, nt, sp.total, s>>>(DUMP_ARGS);
-    }
-#undef DUMP_ARGS
+    const cudaError_t e = with_shape(cfg.shape, prm.k_moves > 1, [&](auto sh, auto ch) {
+        using SH = decltype(sh);
+        score_dump_kernel<SH, decltype(ch)::value><<<grid, nt, sp.total, s>>>(
+            d_meta, inst, use_best, iter, tmax_star, i0, n, identity, prm, sp, d_cost, d_tmax, d_moves, d_nhu, d_nsu,
+            d_tcompl, d_twait, d_tcost, d_hu_tour, d_su_tour);
+        return cudaSuccess;
+    });
+    if (e != cudaSuccess) return e;
     return cudaGetLastError();
 }
 
@@ -2853,19 +3210,12 @@ cudaError_t launch_decode(const LaunchCfg &cfg, const InstMeta *d_meta, int32_t 
     int grid = (n + nt - 1) / nt;
     if (grid > cfg.grid) grid = cfg.grid;
     if (grid < 1) grid = 1;
-    switch (cfg.shape) {
-    case SHAPE_T4_S64_DSMEM:
-        decode_kernel<ShapeA><<<grid, nt, sp.total, s>>>(d_meta, inst, use_best, iter, d_idx, n, prm, sp, d_plans);
-        break;
-    case SHAPE_T6_S64_GMEM:
-        decode_kernel<ShapeB><<<grid, nt, sp.total, s>>>(d_meta, inst, use_best, iter, d_idx, n, prm, sp, d_plans);
-        break;
-    case SHAPE_T10_S128_GMEM:
-        decode_kernel<ShapeD><<<grid, nt, sp.total, s>>>(d_meta, inst, use_best, iter, d_idx, n, prm, sp, d_plans);
-        break;
-    default:
-        decode_kernel<ShapeC><<<grid, nt, sp.total, s>>>(d_meta, inst, use_best, iter, d_idx, n, prm, sp, d_plans);
-    }
+    const cudaError_t e = with_shape(cfg.shape, prm.k_moves > 1, [&](auto sh, auto ch) {
+        decode_kernel<decltype(sh), decltype(ch)::value><<<grid, nt, sp.total, s>>>(d_meta, inst, use_best, iter,
+                                                                                   d_idx, n, prm, sp, d_plans);
+        return cudaSuccess;
+    });
+    if (e != cudaSuccess) return e;
     return cudaGetLastError();
 }
 

@@ -12,11 +12,12 @@ REL_TOL = 1e-5
 TAU = 1e-5
 
 
-def pair(inst, n_cand, eps=0.5, seed=1000, gate=1, p_swap=0.0, fix_field_bp=0, fix_resources=0, inst_idx=0, **kw):
+def pair(inst, n_cand, eps=0.5, seed=1000, gate=1, p_swap=0.0, fix_field_bp=0, fix_resources=0, inst_idx=0,
+         k_moves=1, **kw):
     p = biolog.make_params(n_cand=n_cand, eps=eps, seed=seed, gate=gate, p_swap=p_swap, fix_field_bp=fix_field_bp,
-                           fix_resources=fix_resources, inst_idx=inst_idx, **kw)
+                           fix_resources=fix_resources, inst_idx=inst_idx, k_moves=k_moves, **kw)
     op = O.make_params(eps=eps, seed=seed, gate=gate, p_swap=p_swap, fix_field_bp=fix_field_bp,
-                       fix_resources=fix_resources, inst_idx=inst_idx)
+                       fix_resources=fix_resources, inst_idx=inst_idx, k_moves=k_moves)
     return biolog.Search([inst], p), O.Oracle(inst), op
 
 

@@ -85,3 +85,15 @@ def test_argmin_noalloc_size_checks_without_gpu(lib):
     # legal sizes reach the handle check (NULL handle -> BL_EINVAL), the last ones end at INT32_MAX
     for i0, n in ((0, 1), (0, max_cand), (int32_max - 10, 10), (int32_max - 1, 1), (int32_max - max_cand, max_cand)):
         assert call(i0, n) == biolog.BL_EINVAL, (i0, n)
+
+
+def test_chained_move_parameters_without_gpu(lib):
+    """k_moves: 1 to 3 chained moves are accepted; more, or chained moves with lane groups, are not."""
+    inst = I.make_instance("paper", 0)
+    for k in (0, 1, 2, 3):
+        assert biolog.workspace_bytes([inst], biolog.make_params(n_cand=4096, k_moves=k)) > 0
+    for p in (biolog.make_params(n_cand=4096, k_moves=4), biolog.make_params(n_cand=4096, k_moves=-1),
+              biolog.make_params(n_cand=4096, k_moves=2, lanes_per_cand=8)):
+        with pytest.raises(biolog.BiologError) as e:
+            biolog.workspace_bytes([inst], p)
+        assert e.value.code == biolog.BL_EINVAL
