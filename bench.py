@@ -38,6 +38,8 @@ UNIT = "candidates/s"
 WORKLOAD = "paper-scale plain search: 40 fields, 5 BPs, 3 tours, 10 HUs, 20 SUs, 50x50 km, 2^20 candidates/iter"
 WORKLOAD_BATCHED = ("batched uneven instances: 256 instances (fields U{10..120}, BPs U{2..10}, tours U{1..6}, "
                     "HUs U{2..20}, SUs U{4..40}), 2^16 candidates/instance/iter, one launch per iteration")
+WORKLOAD_LARGE = ("large plain search: 300 fields, 20 BPs, 10 tours, 60 HUs, 120 SUs, 150x150 km, "
+                  "2^24 candidates/iter")
 L2_FLUSH_BYTES = 256 << 20
 # time-to-1% study settings per workload (paper: seeds 0-9, the paper's 10 experiments)
 STUDY = {
@@ -47,6 +49,13 @@ STUDY = {
                   pool=1 << 18, keep=2359, rand_frac=0.001, train_seeds=range(100, 104), train_iters=30,
                   ref_n=1 << 16),
 }
+
+
+# the wall-clock time-to-1% study on the large workload (the default line's time_to_1pct key): plain and
+# batched search with one and two chained moves per candidate, and learned + batched
+STUDY_WALL = dict(workload="large", seeds=range(5), n=1 << 20, n_batched=1 << 16, max_iters=400, ref_iters=4000,
+                  ref_n=1 << 16, pool=1 << 18, keep=2359, rand_frac=0.001, train_seeds=range(100, 104),
+                  train_iters=30, k_values=(1, 2))
 
 
 def _dist():
@@ -473,6 +482,8 @@ def main():
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--no-time-to-target", action="store_true",
                     help="skip the time-to-1%% study (paper workload, rank 0, one GPU)")
+    ap.add_argument("--no-extra-lines", action="store_true",
+                    help="skip the batched and large lines that the default (paper) line carries")
     ap.add_argument("--study", action="store_true", help="print only the time-to-1%% study for --workload")
     ap.add_argument("--ref-budget", type=float, default=120.0, help="seconds of oracle work in --impl reference")
     args = ap.parse_args()
@@ -494,19 +505,56 @@ def main():
                               **time_to_target.study(**STUDY[args.workload]))), flush=True)
         return
 
+    import torch
+
+    torch.cuda.set_device(local)
+    line = measure_plain(args, args.workload, ws, rank, local, args.cpu_budget)
+    if rank == 0:
+        if ws == 1 and args.workload == "paper" and not args.no_extra_lines:
+            # the other single-GPU workloads, each with its own roofline, e2e and CPU baseline
+            for wl in ("batched", "large"):
+                sub = measure_plain(args, wl, ws, rank, local, args.cpu_budget / 2)
+                line[wl] = {k: sub[k] for k in ("value", "unit", "ms_per_step", "config", "gpu_launches", "clocks",
+                                                "e2e", "roofline", "cpu_baseline") if k in sub}
+        if ws == 1 and args.workload == "paper" and not args.no_time_to_target:
+            from paper_1909_10286_gb300 import time_to_target
+
+            r = time_to_target.study_wall(**STUDY_WALL)
+            line["time_to_1pct"] = {
+                "unit": "ms", "higher_is_better": False, "workload": WORKLOAD_LARGE, "tol": r["tol"],
+                "instances": r["seeds"], "timing": r["timing"],
+                "c_ref": f"best C* of a plain batched run of {r['c_ref_run']['iters']} iterations of "
+                         f"{r['c_ref_run']['n_cand']} candidates per instance",
+                "median_ms": {k: f["median_ms"] for k, f in r["forms"].items()},
+                "all_instances_ms": {k: f["all_instances_ms"] for k, f in r["forms"].items()},
+                "reached": {k: f["reached"] for k, f in r["forms"].items()},
+                "iters_to_target": {k: f["iters"] for k, f in r["forms"].items()},
+                "setup_s": {k: f["setup_s"] for k, f in r["forms"].items()},
+                "forms": {k: {q: v for q, v in f.items() if q in ("n_cand", "k_moves", "pool", "keep", "rand_frac")}
+                          for k, f in r["forms"].items()},
+                "ranker_training": {k: r["forms"]["learned_batched"][k]
+                                    for k in ("train_tuples", "train_s", "train_loss_first_last")}}
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+def measure_plain(args, workload, ws, rank, local, cpu_budget):
+    """One plain-search line: device-timed throughput, e2e through the C ABI, and on rank 0 the
+    roofline and the CPU baseline."""
     import numpy as np
     import torch
 
     from paper_1909_10286_gb300 import biolog
     from paper_1909_10286_gb300 import instances as I
 
-    torch.cuda.set_device(local)
-    n = args.n_cand or I.SEARCH[args.workload][0]
+    n = (args.n_cand if workload == args.workload else 0) or I.SEARCH[workload][0]
     kw = dict(eps=0.5, seed=1000 + args.seed + rank, gate=1)
     stream = torch.cuda.Stream()
     tuned = None
-    insts = rank_instances(args.workload, args.seed, rank, args.n_inst)
-    if args.workload == "batched":
+    insts = rank_instances(workload, args.seed, rank, args.n_inst)
+    if workload == "batched":
         if args.no_autotune:
             params = biolog.make_params(n_cand=n, **kw)
         else:
@@ -542,33 +590,43 @@ def main():
     t_ms = _max_over_ranks(t_ms, ws)
     value = n_total * args.steps * ws / (t_ms / 1e3)
     ms_step = t_ms / args.steps
+    del flush
 
     # e2e through the C ABI: state in from pinned host memory, one iteration, state out
     st = S.get_state()
-    pin = {k: [torch.from_numpy(np.ascontiguousarray(a)).pin_memory() for a in st[k]] for k in ("xold", "xbest")}
-    hstate = dict(xold=[t.numpy() for t in pin["xold"]], xbest=[t.numpy() for t in pin["xbest"]],
-                  cstar=st["cstar"], tmaxstar=st["tmaxstar"], iter=st["iter"])
-    bytes_state = sum(a.nbytes for a in hstate["xold"] + hstate["xbest"]) + 12
+    n_inst = len(insts)
+    pin = [{k: [torch.from_numpy(np.ascontiguousarray(a)).pin_memory() for a in S.get_state(inst=q)[k]]
+            for k in ("xold", "xbest")} for q in range(n_inst)]
+    hstate = []
+    for q in range(n_inst):
+        sq = S.get_state(inst=q)
+        hstate.append(dict(xold=[t.numpy() for t in pin[q]["xold"]], xbest=[t.numpy() for t in pin[q]["xbest"]],
+                           cstar=sq["cstar"], tmaxstar=sq["tmaxstar"], iter=sq["iter"]))
+    bytes_state = sum(sum(a.nbytes for a in h["xold"] + h["xbest"]) + 12 for h in hstate)
+    e2e_steps = max(1, min(args.e2e_steps, int(2000 / max(ms_step, 1e-3))))
     _barrier(ws)
     t0 = time.perf_counter()
-    for _ in range(args.e2e_steps):
-        S.set_state(hstate)
+    for _ in range(e2e_steps):
+        for q in range(n_inst):
+            S.set_state(hstate[q], inst=q)
         with torch.cuda.stream(stream):
             S.search_step(1)
-        out = S.get_state()
-        for k in ("xold", "xbest"):
-            for dst, src in zip(hstate[k], out[k]):
-                dst[...] = src
-        hstate.update(cstar=out["cstar"], tmaxstar=out["tmaxstar"], iter=out["iter"])
+        for q in range(n_inst):
+            out = S.get_state(inst=q)
+            for k in ("xold", "xbest"):
+                for dst, src in zip(hstate[q][k], out[k]):
+                    dst[...] = src
+            hstate[q].update(cstar=out["cstar"], tmaxstar=out["tmaxstar"], iter=out["iter"])
     e2e_s = _max_over_ranks(time.perf_counter() - t0, ws)
-    e2e = {"value": n_total * args.e2e_steps * ws / e2e_s, "unit": UNIT, "h2d_bytes_per_step": bytes_state,
-           "d2h_bytes_per_step": bytes_state,
-           "api": "bl_set_state + bl_search_step(1) + bl_get_state, pinned host buffers"}
+    e2e = {"value": n_total * e2e_steps * ws / e2e_s, "unit": UNIT, "h2d_bytes_per_step": bytes_state,
+           "d2h_bytes_per_step": bytes_state, "steps": e2e_steps,
+           "api": "bl_set_state + bl_search_step(1) + bl_get_state per instance, pinned host buffers"}
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": {"paper": WORKLOAD, "batched": WORKLOAD_BATCHED}.get(args.workload, args.workload),
+            "config": {"workload": {"paper": WORKLOAD, "batched": WORKLOAD_BATCHED,
+                                    "large": WORKLOAD_LARGE}.get(workload, workload),
                        "instance_seed": args.seed, "n_instances": len(insts), "n_cand_per_iter": n_total,
                        "eps": 0.5, "gate": 1, "autotuned": tuned,
                        "l2": "flushed before every timed step (256 MiB device write)",
@@ -593,40 +651,18 @@ def main():
         peak = sms * 4 * 32 * f_mhz * 1e6 / 1e12            # lane-ops/s: 4 schedulers x 32 lanes per SM
         achieved = w_per * n_total / (ms_step / 1e3) / 1e12
         line["roofline"] = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tlane-op/s",
-                            "frac": achieved / peak, "traffic": _traffic(args.workload), "ops_per_candidate": w_per,
+                            "frac": achieved / peak, "traffic": _traffic(workload), "ops_per_candidate": w_per,
                             "peak_basis": f"{sms} SMs x 4 schedulers x 32 lanes x {f_mhz:.0f} MHz (sm_max_mhz of "
                                           "MEASURED_PEAKS.json)"}
         if len(insts) > 1:
             line["roofline"]["ops_per_candidate_basis"] = "oracle count on instance 0 of the batch"
         if ws == 1 and not args.no_cpu_baseline:
-            rate, m_s, iters, thr = oracle_throughput(inst, kw, n, args.cpu_budget, os.cpu_count() or 1)
+            rate, m_s, iters, thr = oracle_throughput(inst, kw, n, cpu_budget, os.cpu_count() or 1)
             line["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": thr, "kind": "oracle",
                                     "sample": f"{iters} oracle iterations of {m_s} candidates (of {n}) from the "
-                                              "initial plan"}
-        S.close()
-        if ws == 1 and args.workload == "paper" and not args.no_time_to_target:
-            from paper_1909_10286_gb300 import time_to_target
-
-            r = time_to_target.study(**STUDY["paper"])
-            line["time_to_1pct"] = {
-                "unit": "ms", "higher_is_better": False, "tol": r["tol"], "instances": r["seeds"],
-                "c_ref": "best C* of a plain run of 10x the 1000-iteration budget, 2^20 candidates/iter",
-                "median_ms": {k: f["median_ms"] for k, f in r["forms"].items()},
-                "all_instances_ms": {k: f["all_instances_ms"] for k, f in r["forms"].items()},
-                "ms_per_iter": {k: f["ms_per_iter"] for k, f in r["forms"].items()},
-                "iters_to_target": {k: f["iters"] for k, f in r["forms"].items()},
-                "forms": {"plain": "one instance per handle, 2^20 candidates/iter",
-                          "batched": "10 instances in one handle, 2^16 candidates/instance/iter",
-                          "learned_batched": "10 instances in one handle; per instance 2^16 Philox moves ranked "
-                                             "by the MLP, ~7373 best + 1.4% random scored exactly"},
-                "ranker_training": {k: r["forms"]["learned_batched"][k]
-                                    for k in ("train_tuples", "train_s", "train_loss_first_last")}}
-        print(json.dumps(line), flush=True)
-    else:
-        S.close()
-    if ws > 1:
-        import torch.distributed as dist
-        dist.destroy_process_group()
+                                              "initial plan" + (" of instance 0" if len(insts) > 1 else "")}
+    S.close()
+    return line
 
 
 if __name__ == "__main__":
