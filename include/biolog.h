@@ -103,6 +103,9 @@ typedef struct bl_params {
                                 2 or 3: Step 8 repeated, move j drawn on the plan the first j
                                 moves made (Philox counter word 3 = 0, then j + 1); needs
                                 lanes_per_cand <= 1 and no learned proposals (else BL_EINVAL) */
+    uint32_t cand_offset;    /* candidate numbers (Philox counter word 0) of this handle:
+                                cand_offset .. cand_offset + n_cand - 1 (0 = the whole range);
+                                one slice of a split iteration (bl_search_score_slice) */
     void *workspace;         /* device, optional: caller-owned buffer of
                                 bl_workspace_bytes() bytes, 256-byte aligned; NULL = the
                                 library allocates and frees its own */
@@ -167,6 +170,24 @@ int bl_plan_init_batch(const bl_instance *insts, int32_t n_inst, const bl_params
    of x_old, x*, C*, Tmax*. Launches are replayed from a CUDA graph. Device
    errors (BL_ETIMEOUT) surface at the next synchronising call. */
 int bl_search_step(bl_handle *h, int32_t n_iters);
+
+/* One iteration split over several handles -- on several GPUs, one process
+   each (Sec. 2.5: the candidates of an iteration are independent). Every
+   handle holds the same instance, parameters and state, and scores its own
+   slice of the candidate numbers (params.cand_offset, params.n_cand).
+   bl_search_score_slice runs Steps 9-12 on the slice and writes the slice's
+   argmin key ((cost bits << 32) | i, the same order as bl_get_log's i*) to
+   *d_key (device memory, caller-owned), without updating anything. The
+   caller reduces the slices' keys to their minimum (an all-reduce-min of
+   one 64-bit integer per iteration) and passes the result to
+   bl_search_apply on every handle, which replays move i* on the handle's own
+   copy of the base plan, recomputes Tmax_{i*} and runs Steps 13-16, so all
+   handles keep identical states without exchanging plans. Both are
+   asynchronous on the handle's stream; one instance per handle (BL_EINVAL
+   otherwise). A key that does not score as candidate i* of this iteration
+   makes the handle's next synchronising call return BL_ESTATE. */
+int bl_search_score_slice(bl_handle *h, uint64_t *d_key);
+int bl_search_apply(bl_handle *h, const uint64_t *d_key);
 
 /* Inspection of the search kernel itself (Steps 9-12 of Algorithm 1, the
    three evaluation steps of Sec. 2.5): one iteration exactly as

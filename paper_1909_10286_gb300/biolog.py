@@ -25,7 +25,7 @@ BL_OK, BL_EINVAL, BL_EINFEASIBLE_INSTANCE, BL_ETOO_LARGE, BL_ECUDA, BL_ETIMEOUT,
 EXPORTS = ("bl_workspace_bytes", "bl_plan_init", "bl_plan_init_batch", "bl_search_step", "bl_best_plan",
            "bl_get_state", "bl_set_state", "bl_get_log", "bl_score_candidates", "bl_decode_candidates",
            "bl_get_config", "bl_plan_free", "bl_last_error", "bl_global_error", "bl_argmin_noalloc", "bl_wait_selftest",
-           "bl_search_step_inspect",
+           "bl_search_step_inspect", "bl_search_score_slice", "bl_search_apply",
            "bl_mlp_create", "bl_mlp_forward", "bl_mlp_grads", "bl_mlp_train_step", "bl_mlp_get", "bl_mlp_set",
            "bl_mlp_free", "bl_mlp_last_error", "bl_gemm_bf16", "bl_features", "bl_search_step_learned")
 
@@ -49,7 +49,7 @@ class bl_params(C.Structure):
                 ("n_cand", C.c_int32), ("fix_field_bp", C.c_int32), ("fix_resources", C.c_int32),
                 ("gate", C.c_int32), ("block_threads", C.c_int32), ("blocks_per_sm", C.c_int32), ("tile", C.c_int32),
                 ("log_capacity", C.c_int32), ("lanes_per_cand", C.c_int32), ("k_moves", C.c_int32),
-                ("workspace", C.c_void_p),
+                ("cand_offset", C.c_uint32), ("workspace", C.c_void_p),
                 ("workspace_bytes", C.c_size_t)]
 
 
@@ -84,6 +84,8 @@ def load(path: str | None = None):
             L.bl_plan_init_batch.argtypes = [C.POINTER(bl_instance), C.c_int32, C.POINTER(bl_params), vp, C.POINTER(vp)]
             L.bl_search_step.argtypes = [vp, C.c_int32]
             L.bl_search_step_inspect.argtypes = [vp, vp, C.c_int32]
+            L.bl_search_score_slice.argtypes = [vp, vp]
+            L.bl_search_apply.argtypes = [vp, vp]
             L.bl_best_plan.argtypes = [vp, C.c_int32, C.POINTER(bl_plan)]
             L.bl_get_state.argtypes = [vp, C.c_int32, C.POINTER(bl_state)]
             L.bl_set_state.argtypes = [vp, C.c_int32, C.POINTER(bl_state)]
@@ -131,10 +133,10 @@ class _InstanceArgs:
 def make_params(n_cand: int, eps: float = 0.5, seed: int = 0, inst_idx: int = 0, fix_field_bp: int = 0,
                 fix_resources: int = 0, gate: int = 1, p_swap: float = 0.0, block_threads: int = 0,
                 blocks_per_sm: int = 0, tile: int = 0, log_capacity: int = 0, lanes_per_cand: int = 0,
-                k_moves: int = 1) -> bl_params:
+                k_moves: int = 1, cand_offset: int = 0) -> bl_params:
     return bl_params(float(eps), float(p_swap), int(seed), int(inst_idx), int(n_cand), int(fix_field_bp),
                      int(fix_resources), int(gate), int(block_threads), int(blocks_per_sm), int(tile),
-                     int(log_capacity), int(lanes_per_cand), int(k_moves), None, 0)
+                     int(log_capacity), int(lanes_per_cand), int(k_moves), int(cand_offset), None, 0)
 
 
 def _check(rc: int, handle=None):
@@ -185,6 +187,15 @@ class Search:
     # --- the three calls of the paper's loop
     def search_step(self, n_iters: int):
         _check(load().bl_search_step(self.h, int(n_iters)), self.h)
+
+    def score_slice(self, d_key_ptr: int):
+        """bl_search_score_slice: this handle's slice of the iteration, its argmin key into 8 bytes of device
+        memory at d_key_ptr (e.g. an int64 CUDA tensor's data_ptr())."""
+        _check(load().bl_search_score_slice(self.h, C.c_void_p(d_key_ptr)), self.h)
+
+    def apply(self, d_key_ptr: int):
+        """bl_search_apply: Steps 13-16 with the iteration's reduced argmin key (device memory)."""
+        _check(load().bl_search_apply(self.h, C.c_void_p(d_key_ptr)), self.h)
 
     def search_step_inspect(self, out, stride: int):
         """bl_search_step_inspect: one iteration of the search kernel that also writes {C_i, Tmax_i}

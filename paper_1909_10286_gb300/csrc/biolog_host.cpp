@@ -475,17 +475,27 @@ void plan_work(bl_handle *h, int sms, int blocks_per_sm)
     }
 }
 
+// A device-side error flag: 1 = a bounded wait gave up, 2 = a split iteration's reduced key did not
+// score as this iteration's candidate. Either way the handle refuses further work.
+int state_error(bl_handle *h, uint32_t code, int inst)
+{
+    h->failed = true;
+    if (code == 2) {
+        h->err = "bl_search_apply: the key is not the argmin of this iteration's slices (instance " +
+                 std::to_string(inst) + ")";
+        return BL_ESTATE;
+    }
+    h->err = "a bounded device wait gave up (instance " + std::to_string(inst) + ")";
+    return BL_ETIMEOUT;
+}
+
 int sync_and_check(bl_handle *h)
 {
     CK(h, cudaStreamSynchronize(h->stream));
     for (int i = 0; i < h->n_inst; ++i) {
         InstState st;
         CK(h, cudaMemcpy(&st, h->at<InstState>(h->ws.state[(size_t)i]), sizeof(st), cudaMemcpyDeviceToHost));
-        if (st.error) {
-            h->err = "a bounded device wait gave up (instance " + std::to_string(i) + ")";
-            h->failed = true;
-            return BL_ETIMEOUT;
-        }
+        if (st.error) return state_error(h, st.error, i);
     }
     return BL_OK;
 }
@@ -534,6 +544,10 @@ int init_common(const bl_instance *insts, int32_t n_inst, const bl_params *param
         g_error = "k_moves must be in [0, " + std::to_string(kMaxMoves) + "]";
         return BL_EINVAL;
     }
+    if ((int64_t)params->cand_offset + (int64_t)params->n_cand > (int64_t)INT32_MAX) {
+        g_error = "cand_offset + n_cand must not exceed INT32_MAX";
+        return BL_EINVAL;
+    }
     if (params->k_moves > 1 && params->lanes_per_cand > 1) {
         g_error = "chained moves (k_moves > 1) are scored one thread per candidate: lanes_per_cand must be <= 1";
         return BL_EINVAL;
@@ -551,6 +565,8 @@ int init_common(const bl_instance *insts, int32_t n_inst, const bl_params *param
     h->sp.fix_resources = params->fix_resources;
     h->sp.gate = params->gate;
     h->sp.k_moves = params->k_moves <= 1 ? 1 : params->k_moves;
+    h->sp.cand_offset = params->cand_offset;
+    h->sp.defer_update = 0;
     h->insts.resize((size_t)n_inst);
     for (int i = 0; i < n_inst; ++i) {
         std::string err;
@@ -842,6 +858,30 @@ int bl_search_step_inspect(bl_handle *h, float *d_out, int32_t stride)
     return BL_OK;
 }
 
+int bl_search_score_slice(bl_handle *h, uint64_t *d_key)
+{
+    if (!h || !d_key) return BL_EINVAL;
+    if (h->failed) return BL_ESTATE;
+    if (h->n_inst != 1) { h->err = "split iterations search one instance per handle"; return BL_EINVAL; }
+    SearchParams sp = h->sp;
+    sp.defer_update = 1;
+    CK(h, launch_search_iteration(h->cfg, h->at<InstMeta>(h->ws.meta), h->at<WorkItem>(h->ws.work),
+                                  (int32_t)h->work.size(), sp, h->at<unsigned long long>(h->ws.slot_key),
+                                  h->at<float>(h->ws.slot_tmax), h->at<int32_t>(h->ws.slot_base), h->stream));
+    CK(h, cudaMemcpyAsync(d_key, &h->meta[0].state->key, sizeof(uint64_t), cudaMemcpyDeviceToDevice, h->stream));
+    return BL_OK;
+}
+
+int bl_search_apply(bl_handle *h, const uint64_t *d_key)
+{
+    if (!h || !d_key) return BL_EINVAL;
+    if (h->failed) return BL_ESTATE;
+    if (h->n_inst != 1) { h->err = "split iterations search one instance per handle"; return BL_EINVAL; }
+    CK(h, launch_apply_key(h->cfg, h->at<InstMeta>(h->ws.meta), h->sp,
+                           reinterpret_cast<const unsigned long long *>(d_key), h->stream));
+    return BL_OK;
+}
+
 int bl_get_state(bl_handle *h, int32_t inst, bl_state *out)
 {
     if (!h || !out || inst < 0 || inst >= h->n_inst) return BL_EINVAL;
@@ -860,11 +900,7 @@ int bl_get_state(bl_handle *h, int32_t inst, bl_state *out)
     InstState st;
     CK(h, cudaMemcpyAsync(&st, M.state, sizeof(st), cudaMemcpyDeviceToHost, h->stream));
     CK(h, cudaStreamSynchronize(h->stream));
-    if (st.error) {
-        h->err = "a bounded device wait gave up";
-        h->failed = true;
-        return BL_ETIMEOUT;
-    }
+    if (st.error) return state_error(h, st.error, inst);
     out->cstar = st.cstar;
     out->tmaxstar = st.tmaxstar;
     out->iter = st.iter;
@@ -1040,6 +1076,7 @@ int bl_search_step_learned(bl_handle *h, bl_mlp *mlp, int32_t n_iters, int32_t p
         return BL_EINVAL;
     if (h->failed) return BL_ESTATE;
     if (h->sp.k_moves > 1) { h->err = "learned proposals rank one-move candidates only"; return BL_EINVAL; }
+    if (h->sp.cand_offset != 0) { h->err = "learned proposals rank the pool from candidate 0"; return BL_EINVAL; }
     if (mlp_stream_of(mlp) != h->stream) {
         h->err = "learned proposals: create the MLP on the search handle's stream";
         return BL_EINVAL;

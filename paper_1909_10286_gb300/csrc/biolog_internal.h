@@ -89,6 +89,8 @@ struct SearchParams {
     int32_t fix_resources;
     int32_t gate;
     int32_t k_moves;           // moves chained per candidate (Step 8 repeated), 1..kMaxMoves
+    uint32_t cand_offset;      // candidate numbers of this handle: cand_offset + [0, n_cand)
+    int32_t defer_update;      // 1: the iteration only leaves its argmin key in InstState::key
 };
 constexpr int kMaxMoves = 3;
 
@@ -137,6 +139,8 @@ cudaError_t launch_score_dump(const LaunchCfg &cfg, const InstMeta *d_meta, int3
 cudaError_t launch_decode(const LaunchCfg &cfg, const InstMeta *d_meta, int32_t inst, int32_t use_best,
                           uint32_t iter, const int32_t *d_idx, int32_t n, SearchParams prm, int16_t *d_plans,
                           cudaStream_t s);
+cudaError_t launch_apply_key(const LaunchCfg &cfg, const InstMeta *d_meta, SearchParams prm,
+                             const unsigned long long *d_key, cudaStream_t s);
 cudaError_t noalloc_scratch_address(void **ptr);
 cudaError_t launch_argmin_noalloc(const LaunchCfg &cfg, const InstMeta *d_meta, int32_t inst, int32_t use_best,
                                   uint32_t iter, float tmax_star, int32_t i0, int32_t n, SearchParams prm,

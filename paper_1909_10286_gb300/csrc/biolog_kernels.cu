@@ -1521,6 +1521,50 @@ __device__ void write_plan_chain(const Ctx &c, const ChainView &cv, int16_t *out
 // warps) into its slot; the last work item of the instance to finish takes the
 // argmin over the instance's slots and runs Steps 13-16 (replay the move,
 // update x_old, x*, C*, Tmax*, the log and the iteration counter).
+// Steps 13-16 of one instance with the iteration's argmin key bk (cost bits << 32 | i*) and the
+// winner's Tmax bt: replay move(s) i* on the staged base into x_old (x_old <- base if no candidate
+// is feasible), update x*, C*, Tmax* if C_{i*} < C*, log the iteration and advance the counter.
+// One thread.
+template <bool CHAIN>
+__device__ void apply_update(const Ctx &c, const SearchParams &prm, const InstMeta &M, int use_best, uint32_t iter,
+                             unsigned long long bk, float bt)
+{
+    const uint32_t istar = (uint32_t)(bk & 0xffffffffu);
+    const float cst = __uint_as_float((uint32_t)(bk >> 32));
+    InstState *st = M.state;
+    int ind = 0;
+    if (isfinite(cst)) {
+        int kind0;
+        if constexpr (CHAIN) {
+            ChainView cv;
+            draw_chain(c, prm, istar, iter, M.inst_idx, cv);
+            write_plan_chain(c, cv, M.xold);
+            kind0 = cv.L[0].kind;
+        } else {
+            const MoveRec m = draw_move(c, prm, istar, iter, M.inst_idx);
+            write_plan(c, m, M.xold);
+            kind0 = m.kind;
+        }
+        if (cst < st->cstar) {
+            for (int k = 0; k < M.plan_len; ++k) M.xbest[k] = M.xold[k];
+            st->cstar = cst;
+            st->tmaxstar = bt;
+            ind = (kind0 == 0 || kind0 == 2) ? 1 : 2;   // the (first) move's type (Fig. 3)
+        }
+    } else {
+        const int16_t *pl = c.bp_order;
+        for (int k = 0; k < M.plan_len; ++k) M.xold[k] = pl[k];
+    }
+    const int li = (int)(iter % (uint32_t)M.log_cap);
+    M.log_istar[li] = (int32_t)istar;
+    M.log_cistar[li] = cst;
+    M.log_usebest[li] = (int8_t)use_best;
+    M.log_cstar[li] = st->cstar;
+    M.log_ind[li] = (int8_t)ind;
+    st->iter = iter + 1;
+    st->done = 0;
+}
+
 template <int NT, bool CHAIN = false>
 __device__ __forceinline__ void block_argmin_finalize(unsigned long long best, float best_t, BlockShared &bs,
                                                       const InstMeta &M, const WorkItem &wi,
@@ -1575,40 +1619,12 @@ __device__ __forceinline__ void block_argmin_finalize(unsigned long long best, f
                 if (ok < bk) { bk = ok; bt = ot; }
             }
             if (tid == 0) {
-                const uint32_t istar = (uint32_t)(bk & 0xffffffffu);
-                const float cst = __uint_as_float((uint32_t)(bk >> 32));
-                InstState *st = M.state;
-                int ind = 0;
-                if (isfinite(cst)) {
-                    int kind0;
-                    if constexpr (CHAIN) {
-                        ChainView cv;
-                        draw_chain(c, prm, istar, iter, M.inst_idx, cv);
-                        write_plan_chain(c, cv, M.xold);
-                        kind0 = cv.L[0].kind;
-                    } else {
-                        const MoveRec m = draw_move(c, prm, istar, iter, M.inst_idx);
-                        write_plan(c, m, M.xold);
-                        kind0 = m.kind;
-                    }
-                    if (cst < st->cstar) {
-                        for (int k = 0; k < M.plan_len; ++k) M.xbest[k] = M.xold[k];
-                        st->cstar = cst;
-                        st->tmaxstar = bt;
-                        ind = (kind0 == 0 || kind0 == 2) ? 1 : 2;   // the (first) move's type (Fig. 3)
-                    }
+                if (prm.defer_update) {   // a slice of a split iteration: the key waits for the other slices
+                    M.state->key = bk;
+                    M.state->done = 0;
                 } else {
-                    const int16_t *pl = c.bp_order;
-                    for (int k = 0; k < M.plan_len; ++k) M.xold[k] = pl[k];
+                    apply_update<CHAIN>(c, prm, M, bs.use_best, iter, bk, bt);
                 }
-                const int li = (int)(iter % (uint32_t)M.log_cap);
-                M.log_istar[li] = (int32_t)istar;
-                M.log_cistar[li] = cst;
-                M.log_usebest[li] = (int8_t)bs.use_best;
-                M.log_cstar[li] = st->cstar;
-                M.log_ind[li] = (int8_t)ind;
-                st->iter = iter + 1;
-                st->done = 0;
             }
         }
     }
@@ -1703,7 +1719,7 @@ __global__ void __launch_bounds__(SH::NT, SH::MINB) search_iteration_kernel(cons
             int next = c1;   // this warp's next chunk
             if (base < c1) {
                 const int pos = base + lane;
-                const int i = (ilist && pos < c1) ? (int)ilist[pos] : pos;
+                const int i = (ilist && pos < c1) ? (int)ilist[pos] : (int)prm.cand_offset + pos;
                 bool feas = false;
                 MoveRec m = {4, 0, 0, 0};
                 if (pos < c1) {
@@ -1718,7 +1734,7 @@ __global__ void __launch_bounds__(SH::NT, SH::MINB) search_iteration_kernel(cons
                     if (!feas) {
                         const unsigned long long k = make_key(__int_as_float(0x7f800000), (uint32_t)i);
                         if (k < best) { best = k; best_t = __int_as_float(0x7f800000); }
-                        if (ins) ins[i] = make_float2(__int_as_float(0x7f800000), __int_as_float(0x7f800000));
+                        if (ins) ins[i - (int)prm.cand_offset] = make_float2(__int_as_float(0x7f800000), __int_as_float(0x7f800000));
                     }
                 }
                 const unsigned ball = __ballot_sync(0xffffffffu, feas);
@@ -1759,7 +1775,7 @@ __global__ void __launch_bounds__(SH::NT, SH::MINB) search_iteration_kernel(cons
                     if (isinf(r1.cost)) {   // discarded by the gate: C = +inf (Sec. 2.5)
                         const unsigned long long k = make_key(r1.cost, (uint32_t)i);
                         if (k < best) { best = k; best_t = r1.tmax; }
-                        if (ins) ins[i] = make_float2(r1.cost, r1.tmax);
+                        if (ins) ins[i - (int)prm.cand_offset] = make_float2(r1.cost, r1.tmax);
                     } else {
                         kept = true;
                     }
@@ -1811,7 +1827,7 @@ __global__ void __launch_bounds__(SH::NT, SH::MINB) search_iteration_kernel(cons
                                                                         nullptr, nullptr, nullptr, nullptr, &cv);
                     const unsigned long long k = make_key(r.cost, (uint32_t)i);
                     if (k < best) { best = k; best_t = r.tmax; }
-                    if (ins) ins[i] = make_float2(r.cost, r.tmax);
+                    if (ins) ins[i - (int)prm.cand_offset] = make_float2(r.cost, r.tmax);
                 }
                 __syncwarp();
                 q2head = (q2head + take2) & (WQ - 1);
@@ -1824,6 +1840,54 @@ __global__ void __launch_bounds__(SH::NT, SH::MINB) search_iteration_kernel(cons
             base = next;
         }
         block_argmin_finalize<NT, CHAIN>(best, best_t, bs, M, wi, slot_key, slot_tmax, slot_base, c, prm, iter);
+    }
+}
+
+// Steps 13-16 of an iteration whose candidates were scored in slices (bl_search_score_slice) and whose
+// argmin key -- the minimum over the slices' keys, possibly of other processes -- is read from device
+// memory. The winner's Tmax is recomputed by scoring candidate i* again on the same staged base; a key
+// that does not score as this iteration's candidate i* sets error 2. One instance, one block.
+template <class SH, bool CHAIN>
+__global__ void __launch_bounds__(SH::NT) apply_key_kernel(const InstMeta *__restrict__ meta, SearchParams prm,
+                                                           SmemPlan sp, const unsigned long long *__restrict__ d_key)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ BlockShared bs;
+    const int tid = threadIdx.x;
+    if (tid == 0) {
+        mbar_init(&bs.mbar, 1);
+        fence_mbar_init();
+        bs.phase = 0;
+    }
+    __syncthreads();
+    const InstMeta &M = meta[0];
+    Ctx c;
+    if (!stage_instance<SH>(M, bs, smem, sp, prm, -1, 0xffffffffu, c)) return;
+    if (tid == 0) {
+        const unsigned long long bk = *d_key;
+        const float cst = __uint_as_float((uint32_t)(bk >> 32));
+        float bt = 0.f;
+        if (isfinite(cst)) {
+            const uint32_t istar = (uint32_t)(bk & 0xffffffffu);
+            MoveRec m = {4, 0, 0, 0};
+            ChainView cv;
+            bool feas;
+            if constexpr (CHAIN) {
+                draw_chain(c, prm, istar, bs.iter, M.inst_idx, cv);
+                feas = demand_ok_chain(c, cv);
+            } else {
+                m = draw_move(c, prm, istar, bs.iter, M.inst_idx);
+                feas = demand_ok(c, m);
+            }
+            ScoreOut r = {__int_as_float(0x7f800000), 0.f, 0u};
+            if (feas)
+                r = score_candidate<SH, false, false, 0, CHAIN>(c, prm, m, M.state->tmaxstar, smem + sp.off_tour, tid,
+                                                                nullptr, nullptr, nullptr, nullptr, nullptr, nullptr,
+                                                                nullptr, nullptr, nullptr, nullptr, &cv);
+            if (__float_as_uint(r.cost) != (uint32_t)(bk >> 32)) atomicExch(&M.state->error, 2u);
+            bt = r.tmax;
+        }
+        apply_update<CHAIN>(c, prm, M, bs.use_best, bs.iter, bk, bt);
     }
 }
 
@@ -2329,7 +2393,7 @@ __global__ void __launch_bounds__(COOP_NT) search_iteration_coop_kernel(
         unsigned long long best = ~0ull;
         float best_t = 0.f;
         for (int pos = c0 + grp; pos < c1; pos += NG) {
-            const int i = ilist ? (int)ilist[pos] : pos;
+            const int i = ilist ? (int)ilist[pos] : (int)prm.cand_offset + pos;
             const MoveRec m = draw_move(c, prm, (uint32_t)i, iter, M.inst_idx);
             unsigned long long k;
             float t = __int_as_float(0x7f800000);
@@ -2341,7 +2405,7 @@ __global__ void __launch_bounds__(COOP_NT) search_iteration_coop_kernel(
                 k = make_key(__int_as_float(0x7f800000), (uint32_t)i);
             }
             if (k < best) { best = k; best_t = t; }
-            if (ins && gl == 0) ins[i] = make_float2(__uint_as_float((uint32_t)(k >> 32)), t);
+            if (ins && gl == 0) ins[i - (int)prm.cand_offset] = make_float2(__uint_as_float((uint32_t)(k >> 32)), t);
         }
         block_argmin_finalize<COOP_NT>(best, best_t, bs, M, wi, slot_key, slot_tmax, slot_base, c, prm, iter);
     }
@@ -3011,6 +3075,8 @@ static cudaError_t set_attrs_of(size_t smem)
     if (e != cudaSuccess) return e;
     e = cudaFuncSetAttribute(score_dump_kernel<SH, CHAIN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(apply_key_kernel<SH, CHAIN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
     return cudaFuncSetAttribute(decode_kernel<SH, CHAIN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
 }
 
@@ -3076,6 +3142,19 @@ cudaError_t launch_search_iteration(const LaunchCfg &cfg, const InstMeta *d_meta
         search_iteration_kernel<SH, decltype(ch)::value><<<cfg.grid, SH::NT, sp.total, s>>>(
             d_meta, d_work, n_work, prm, sp, slot_key, slot_tmax, slot_base, cand_list, cand_count, list_stride, insp,
             insp_stride);
+        return cudaSuccess;
+    });
+    if (e != cudaSuccess) return e;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_apply_key(const LaunchCfg &cfg, const InstMeta *d_meta, SearchParams prm,
+                             const unsigned long long *d_key, cudaStream_t s)
+{
+    const SmemPlan sp = plan_for(cfg);
+    const cudaError_t e = with_shape(cfg.shape, prm.k_moves > 1, [&](auto sh, auto ch) {
+        using SH = decltype(sh);
+        apply_key_kernel<SH, decltype(ch)::value><<<1, SH::NT, sp.total, s>>>(d_meta, prm, sp, d_key);
         return cudaSuccess;
     });
     if (e != cudaSuccess) return e;

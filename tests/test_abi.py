@@ -97,3 +97,12 @@ def test_chained_move_parameters_without_gpu(lib):
         with pytest.raises(biolog.BiologError) as e:
             biolog.workspace_bytes([inst], p)
         assert e.value.code == biolog.BL_EINVAL
+
+
+def test_candidate_offset_parameter_without_gpu(lib):
+    """cand_offset + n_cand must stay within the 31-bit candidate numbers."""
+    inst = I.make_instance("paper", 0)
+    assert biolog.workspace_bytes([inst], biolog.make_params(n_cand=4096, cand_offset=(1 << 31) - 1 - 4096)) > 0
+    with pytest.raises(biolog.BiologError) as e:
+        biolog.workspace_bytes([inst], biolog.make_params(n_cand=4096, cand_offset=(1 << 31) - 4096))
+    assert e.value.code == biolog.BL_EINVAL
