@@ -54,7 +54,7 @@ STUDY = {
 # the wall-clock time-to-1% study on the large workload (the default line's time_to_1pct key): plain and
 # batched search with one and two chained moves per candidate, and learned + batched
 STUDY_WALL = dict(workload="large", seeds=range(5), n=1 << 20, n_batched=1 << 16, max_iters=400, ref_iters=4000,
-                  ref_n=1 << 16, pool=1 << 18, keep=2359, rand_frac=0.001, train_seeds=range(100, 104),
+                  ref_n=1 << 16, pool=1 << 16, keep=2048, rand_frac=0.005, train_seeds=range(100, 104),
                   train_iters=30, k_values=(1, 2))
 
 

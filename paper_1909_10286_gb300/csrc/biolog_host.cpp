@@ -260,6 +260,7 @@ void build_blob(HostInst &h)
     L.off_hudeal_q = take((size_t)T * T * 8);
     L.off_sudeal_m = take((size_t)T * T * 16);
     L.off_sudeal_q = take((size_t)T * T * 8);
+    L.off_sudeal_c = take((size_t)T * T * 8);
     L.off_hu_id = take((size_t)H * 4);
     L.off_su_id = take((size_t)S * 4);
     L.prefix_bytes = (int32_t)o;
@@ -300,7 +301,7 @@ void build_blob(HostInst &h)
     // round-robin dealing of sorted units over na active tours (Sec. 2.5,
     // "the average number ... assigned to each group")
     std::vector<unsigned long long> hm((size_t)T * T, 0), sm((size_t)T * T * 2, 0);
-    std::vector<long long> hq((size_t)T * T, 0), sq((size_t)T * T, 0);
+    std::vector<long long> hq((size_t)T * T, 0), sq((size_t)T * T, 0), sc((size_t)T * T, 0);
     for (int na = 1; na <= T; ++na) {
         for (int k = 0; k < H; ++k) {
             const size_t j = (size_t)(na - 1) * T + (size_t)(k % na);
@@ -311,12 +312,14 @@ void build_blob(HostInst &h)
             const size_t j = (size_t)(na - 1) * T + (size_t)(k % na);
             sm[j * 2 + (size_t)(k / 64)] |= 1ull << (k % 64);
             sq[j] += sufq[(size_t)k];
+            sc[j] += sucq[(size_t)k];
         }
     }
     put(h.blob, L.off_hudeal_m, hm.data(), hm.size());
     put(h.blob, L.off_hudeal_q, hq.data(), hq.size());
     put(h.blob, L.off_sudeal_m, sm.data(), sm.size());
     put(h.blob, L.off_sudeal_q, sq.data(), sq.size());
+    put(h.blob, L.off_sudeal_c, sc.data(), sc.size());
     put(h.blob, L.off_D, h.Dq.data(), (size_t)N * N);
 }
 
@@ -415,10 +418,11 @@ int pick_shape(const std::vector<HostInst> &insts)
         maxS = std::max(maxS, h.S);
         maxH = std::max(maxH, h.H);
         maxTotal = std::max(maxTotal, h.L.total_bytes);
-        long long a = 0, b = 0;
+        long long a = 0, b = 0, cq = 0;
         for (long long v : h.hurq.m) a += v;
         for (long long v : h.sufq.m) b += v;
-        fits32 = fits32 && a < (1ll << 31) && b < (1ll << 31);
+        for (long long v : h.sucq.m) cq += v;
+        fits32 = fits32 && a < (1ll << 31) && b < (1ll << 31) && cq < (1ll << 31);
     }
     if (maxT <= 4 && maxS <= 32 && maxH <= 32 && fits32 && maxTotal <= kSmemDistLimit) return SHAPE_T4_S64_DSMEM;
     if (maxT <= 6 && maxS <= 64 && maxH <= 64) return SHAPE_T6_S64_GMEM;

@@ -30,6 +30,7 @@ struct BlobLayout {
     int32_t off_hudeal_q;  // i64[T*T] their fixed-point rate sums
     int32_t off_sudeal_m;  // u64[T*T*2] SU masks of the dealing (two words)
     int32_t off_sudeal_q;  // i64[T*T] their fixed-point fill sums
+    int32_t off_sudeal_c;  // i64[T*T] their fixed-point capacity sums
     int32_t off_hu_id;     // i32[H]   HU id at each sorted position
     int32_t off_su_id;     // i32[S]   SU id at each sorted position
     int32_t off_D;         // i32[N*N] distances in fixed point: round(d * dq_inv), row-major

@@ -183,7 +183,7 @@ struct Ctx {
     const float *suinv, *sufill, *rcp;
     const int *sugrp;
     const unsigned long long *hudeal_m, *sudeal_m;
-    const long long *hudeal_q, *sudeal_q;
+    const long long *hudeal_q, *sudeal_q, *sudeal_c;
     const int *hu_id, *su_id;
     float inv_v, rqs, fqs, cqs, dq_inv, dq_scale, aq_scale;
     double cqs_d;
@@ -980,6 +980,8 @@ __device__ ScoreOut score_candidate(const Ctx &c, const SearchParams &p, const M
             const S sq = (S)c.sudeal_q[di + j];
             ts.Saq.set(g, sq);
             const float ir = __fdividef(1.0f, __fmul_rn(to_f(ts.Rq.get(g)), c.rqs));
+            // R(g) is not needed any more: its column holds the tour's SU capacity sum from here on
+            ts.Rq.set(g, (S)c.sudeal_c[di + j]);
             ts.iR.set(g, ir);
             const int st = su_star<SH>(c, m0, m1);
             ts.star.set(g, st);
@@ -1054,6 +1056,7 @@ __device__ ScoreOut score_candidate(const Ctx &c, const SearchParams &p, const M
                 ts.S1.set(gn, n1 & ~(1ull << (k - 64)));
             }
             ts.Saq.set(gx, (S)(sqx + (S)c.sufq[k])); ts.Saq.set(gn, (S)(sqn - (S)c.sufq[k]));
+            ts.Rq.set(gx, (S)(ts.Rq.get(gx) + (S)c.sucq[k])); ts.Rq.set(gn, (S)(ts.Rq.get(gn) - (S)c.sucq[k]));
             ts.star.set(gx, sx); ts.star.set(gn, sn);
 #pragma unroll
             for (int g = 0; g < MAXT; ++g) tv[g] = (g == gx) ? tmx : ((g == gn) ? tmn : tv[g]);
@@ -1077,7 +1080,7 @@ __device__ ScoreOut score_candidate(const Ctx &c, const SearchParams &p, const M
             const M s0 = ts.S0.get(g);
             const unsigned long long s1 = (SW > 1) ? ts.S1.get(g) : 0ull;
             const int nsu = popc_m(s0) + (SW > 1 ? popc_m(s1) : 0);
-            kfv[g] = __fdividef((float)nsu, __fmul_rn(__ll2float_rn(cap_sum<SH>(c, s0, s1)), c.cqs));
+            kfv[g] = __fdividef((float)nsu, __fmul_rn(__ll2float_rn((long long)ts.Rq.get(g)), c.cqs));
             if constexpr (IDENT) o_kf[g] = kfv[g];
         }
     }
@@ -1097,7 +1100,7 @@ __device__ ScoreOut score_candidate(const Ctx &c, const SearchParams &p, const M
         for (int g = 0; g < MAXT; ++g)
             if (((amask >> g) & 1u) && (((moved >> g) & 1u) || kfv[g] != c.kf_base[g])) fresh |= 1u << g;
     }
-    // rare exact path of Eq. 4: capacity sum of tour g recomputed from its SU set
+    // rare exact path of Eq. 4, with the tour's exact capacity sum
     auto ceil_n = [&](int g, float sup, float kf) -> int {
         const float q = __fmul_rn(sup, kf);
         const float rq = rintf(q);
@@ -1105,7 +1108,7 @@ __device__ ScoreOut score_candidate(const Ctx &c, const SearchParams &p, const M
         const M s0 = ts.S0.get(g);
         const unsigned long long s1 = (SW > 1) ? ts.S1.get(g) : 0ull;
         const int nsu = popc_m(s0) + (SW > 1 ? popc_m(s1) : 0);
-        return exact_ceil(sup, nsu, (double)cap_sum<SH>(c, s0, s1) * c.cqs_d, q);
+        return exact_ceil(sup, nsu, (double)ts.Rq.get(g) * c.cqs_d, q);
     };
     long long shq = 0;
     for (int g = 0; g < c.T; ++g) {
@@ -1340,6 +1343,7 @@ __device__ bool stage_base(const InstMeta &M, BlockShared &bs, unsigned char *sm
     c.hudeal_q = (const long long *)(blob + M.L.off_hudeal_q);
     c.sudeal_m = (const unsigned long long *)(blob + M.L.off_sudeal_m);
     c.sudeal_q = (const long long *)(blob + M.L.off_sudeal_q);
+    c.sudeal_c = (const long long *)(blob + M.L.off_sudeal_c);
     c.hu_id = (const int *)(blob + M.L.off_hu_id);
     c.su_id = (const int *)(blob + M.L.off_su_id);
     c.inv_v = M.inv_hu_speed; c.rqs = M.rq_scale; c.fqs = M.fq_scale; c.cqs = M.cq_scale; c.cqs_d = M.cq_scale_d;
