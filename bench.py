@@ -592,35 +592,22 @@ def measure_plain(args, workload, ws, rank, local, cpu_budget):
     ms_step = t_ms / args.steps
     del flush
 
-    # e2e through the C ABI: state in from pinned host memory, one iteration, state out
-    st = S.get_state()
-    n_inst = len(insts)
-    pin = [{k: [torch.from_numpy(np.ascontiguousarray(a)).pin_memory() for a in S.get_state(inst=q)[k]]
-            for k in ("xold", "xbest")} for q in range(n_inst)]
-    hstate = []
-    for q in range(n_inst):
-        sq = S.get_state(inst=q)
-        hstate.append(dict(xold=[t.numpy() for t in pin[q]["xold"]], xbest=[t.numpy() for t in pin[q]["xbest"]],
-                           cstar=sq["cstar"], tmaxstar=sq["tmaxstar"], iter=sq["iter"]))
+    # e2e through the C ABI: every instance's state in from host memory, one iteration, every state
+    # out (bl_set_states / bl_get_states: one transfer each way through the library's pinned staging)
+    hstate = S.get_states()
     bytes_state = sum(sum(a.nbytes for a in h["xold"] + h["xbest"]) + 12 for h in hstate)
     e2e_steps = max(1, min(args.e2e_steps, int(2000 / max(ms_step, 1e-3))))
     _barrier(ws)
     t0 = time.perf_counter()
     for _ in range(e2e_steps):
-        for q in range(n_inst):
-            S.set_state(hstate[q], inst=q)
+        S.set_states(hstate)
         with torch.cuda.stream(stream):
             S.search_step(1)
-        for q in range(n_inst):
-            out = S.get_state(inst=q)
-            for k in ("xold", "xbest"):
-                for dst, src in zip(hstate[q][k], out[k]):
-                    dst[...] = src
-            hstate[q].update(cstar=out["cstar"], tmaxstar=out["tmaxstar"], iter=out["iter"])
+        S.get_states(hstate)
     e2e_s = _max_over_ranks(time.perf_counter() - t0, ws)
     e2e = {"value": n_total * e2e_steps * ws / e2e_s, "unit": UNIT, "h2d_bytes_per_step": bytes_state,
            "d2h_bytes_per_step": bytes_state, "steps": e2e_steps,
-           "api": "bl_set_state + bl_search_step(1) + bl_get_state per instance, pinned host buffers"}
+           "api": "bl_set_states + bl_search_step(1) + bl_get_states (all instances, one transfer each way)"}
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",

@@ -214,6 +214,17 @@ int bl_get_state(bl_handle *h, int32_t inst, bl_state *out);
    are validated; the copy is ordered on the handle's stream. */
 int bl_set_state(bl_handle *h, int32_t inst, const bl_state *in);
 
+/* The same for every instance of the handle at once, in one host<->device
+   transfer each way through a pinned staging buffer the library allocates on
+   first use (a host-driven loop's checkpoint of a batch). out / in point to
+   n_inst states. bl_get_states synchronises; bl_set_states validates every
+   plan first (nothing is written if one is invalid), copies the caller's
+   buffers before it returns, and is asynchronous on the handle's stream.
+   Errors as bl_get_state / bl_set_state, and BL_ETOO_LARGE if the packed
+   states exceed the library's 8 MiB inspection scratch. */
+int bl_get_states(bl_handle *h, bl_state *out);
+int bl_set_states(bl_handle *h, const bl_state *in);
+
 /* Per-iteration log of instance `inst` for iterations [first, first+n) that
    are still in the ring buffer: i*, C_{i*}, whether the base was x* (Eq. 5),
    C* after the update, and the indicator of Fig. 3 (0 no improvement,

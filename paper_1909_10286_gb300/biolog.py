@@ -25,7 +25,7 @@ BL_OK, BL_EINVAL, BL_EINFEASIBLE_INSTANCE, BL_ETOO_LARGE, BL_ECUDA, BL_ETIMEOUT,
 EXPORTS = ("bl_workspace_bytes", "bl_plan_init", "bl_plan_init_batch", "bl_search_step", "bl_best_plan",
            "bl_get_state", "bl_set_state", "bl_get_log", "bl_score_candidates", "bl_decode_candidates",
            "bl_get_config", "bl_plan_free", "bl_last_error", "bl_global_error", "bl_argmin_noalloc", "bl_wait_selftest",
-           "bl_search_step_inspect", "bl_search_score_slice", "bl_search_apply",
+           "bl_search_step_inspect", "bl_search_score_slice", "bl_search_apply", "bl_get_states", "bl_set_states",
            "bl_mlp_create", "bl_mlp_forward", "bl_mlp_grads", "bl_mlp_train_step", "bl_mlp_get", "bl_mlp_set",
            "bl_mlp_free", "bl_mlp_last_error", "bl_gemm_bf16", "bl_features", "bl_search_step_learned")
 
@@ -89,6 +89,8 @@ def load(path: str | None = None):
             L.bl_best_plan.argtypes = [vp, C.c_int32, C.POINTER(bl_plan)]
             L.bl_get_state.argtypes = [vp, C.c_int32, C.POINTER(bl_state)]
             L.bl_set_state.argtypes = [vp, C.c_int32, C.POINTER(bl_state)]
+            L.bl_get_states.argtypes = [vp, vp]
+            L.bl_set_states.argtypes = [vp, vp]
             L.bl_get_log.argtypes = [vp, C.c_int32, C.c_uint32, C.c_int32, vp, vp, vp, vp, vp]
             L.bl_score_candidates.argtypes = [vp, C.c_int32, C.c_int32, C.c_uint32, C.c_float, C.c_int32, C.c_int32,
                                               vp, vp, vp, vp, vp, vp, vp]
@@ -230,6 +232,31 @@ class Search:
         a = [np.ascontiguousarray(x, dtype=np.int16) for x in (*state["xold"], *state["xbest"])]
         s = bl_state(*[_p(x) for x in a], float(state["cstar"]), float(state["tmaxstar"]), int(state["iter"]))
         _check(load().bl_set_state(self.h, int(inst), C.byref(s)), self.h)
+
+    def _state_arrays(self):
+        out = []
+        for I in self.instances:
+            B, T, F = I.n_bps, I.n_tours, I.n_fields
+            a = [np.zeros(n, np.int16) for n in (B, T, F, B, B, T, F, B)]
+            out.append(dict(xold=tuple(a[:4]), xbest=tuple(a[4:]), cstar=0.0, tmaxstar=0.0, iter=0))
+        return out
+
+    def get_states(self, out=None) -> list:
+        """bl_get_states: every instance's state in one transfer; fills and returns `out` (a list of state
+        dicts as get_state returns, e.g. from an earlier call) or new arrays."""
+        out = out if out is not None else self._state_arrays()
+        arr = (bl_state * len(out))(*[bl_state(*[_p(x) for x in (*o["xold"], *o["xbest"])], 0.0, 0.0, 0) for o in out])
+        _check(load().bl_get_states(self.h, C.cast(arr, C.c_void_p)), self.h)
+        for o, s in zip(out, arr):
+            o.update(cstar=s.cstar, tmaxstar=s.tmaxstar, iter=s.iter)
+        return out
+
+    def set_states(self, states: list):
+        """bl_set_states: every instance's state in one transfer."""
+        keep = [[np.ascontiguousarray(x, dtype=np.int16) for x in (*st["xold"], *st["xbest"])] for st in states]
+        arr = (bl_state * len(states))(*[bl_state(*[_p(x) for x in a], float(st["cstar"]), float(st["tmaxstar"]),
+                                                  int(st["iter"])) for a, st in zip(keep, states)])
+        _check(load().bl_set_states(self.h, C.cast(arr, C.c_void_p)), self.h)
 
     def get_log(self, first: int, n: int, inst: int = 0) -> dict:
         o = dict(istar=np.zeros(n, np.int32), c_istar=np.zeros(n, np.float32), use_best=np.zeros(n, np.int8),

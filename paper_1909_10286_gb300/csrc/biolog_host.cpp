@@ -355,6 +355,8 @@ struct bl_handle {
     float *l_y = nullptr, *l_thresh = nullptr;
     uint32_t *l_list = nullptr;
     int32_t *l_count = nullptr;
+    unsigned char *h_states = nullptr;   // pinned staging of bl_get_states / bl_set_states (first use)
+    size_t states_bytes = 0;
     int dev = -1;                      // the device current at plan_init
     void *noalloc_scratch = nullptr;   // device address of bl_argmin_noalloc's static scratch (first call)
     std::string err;
@@ -862,6 +864,120 @@ int bl_search_step_inspect(bl_handle *h, float *d_out, int32_t stride)
     return BL_OK;
 }
 
+namespace {
+// Layout of the packed states: n_inst byte offsets, then per instance x_old, x* and the state record.
+size_t states_layout(const bl_handle *h, std::vector<int32_t> &offs)
+{
+    offs.assign((size_t)h->n_inst, 0);
+    size_t o = align_up(4 * (size_t)h->n_inst, 16);
+    for (int k = 0; k < h->n_inst; ++k) {
+        offs[(size_t)k] = (int32_t)o;
+        o = align_up(o + 4 * (size_t)h->insts[(size_t)k].plan_len + sizeof(InstState), 16);
+    }
+    return o;
+}
+
+int states_staging(bl_handle *h, size_t bytes)
+{
+    if (bytes > kScratchBytes) { h->err = "too many instances for one packed state transfer"; return BL_ETOO_LARGE; }
+    if (h->states_bytes < bytes) {
+        if (h->h_states) cudaFreeHost(h->h_states);
+        h->h_states = nullptr;
+        h->states_bytes = 0;
+        CK(h, cudaMallocHost((void **)&h->h_states, bytes));
+        h->states_bytes = bytes;
+    }
+    return BL_OK;
+}
+}  // namespace
+
+int bl_get_states(bl_handle *h, bl_state *out)
+{
+    if (!h || !out) return BL_EINVAL;
+    if (h->failed) return BL_ESTATE;
+    std::vector<int32_t> offs;
+    const size_t bytes = states_layout(h, offs);
+    int rc = states_staging(h, bytes);
+    if (rc != BL_OK) return rc;
+    // the staging buffer may still feed an earlier bl_set_states copy on the stream
+    CK(h, cudaStreamSynchronize(h->stream));
+    unsigned char *d = h->at<unsigned char>(h->ws.scratch);
+    std::memcpy(h->h_states, offs.data(), 4 * offs.size());
+    CK(h, cudaMemcpyAsync(d, h->h_states, 4 * offs.size(), cudaMemcpyHostToDevice, h->stream));
+    CK(h, launch_state_pack(h->at<InstMeta>(h->ws.meta), h->n_inst, (const int32_t *)d, d, 0, h->stream));
+    CK(h, cudaMemcpyAsync(h->h_states, d, bytes, cudaMemcpyDeviceToHost, h->stream));
+    CK(h, cudaStreamSynchronize(h->stream));
+    for (int k = 0; k < h->n_inst; ++k) {
+        const HostInst &hi = h->insts[(size_t)k];
+        const int B = hi.B, T = hi.T, F = hi.F;
+        const int16_t *p = (const int16_t *)(h->h_states + offs[(size_t)k]);
+        InstState st;
+        std::memcpy(&st, p + 2 * hi.plan_len, sizeof(st));
+        if (st.error) return state_error(h, st.error, k);
+        bl_state &o = out[k];
+        struct Part { int16_t *dst; const int16_t *src; int n; } parts[8] = {
+            {o.xold_bp_order, p, B}, {o.xold_tour_cnt, p + B, T}, {o.xold_field_order, p + B + T, F},
+            {o.xold_bp_cnt, p + B + T + F, B}, {o.xbest_bp_order, p + hi.plan_len, B},
+            {o.xbest_tour_cnt, p + hi.plan_len + B, T}, {o.xbest_field_order, p + hi.plan_len + B + T, F},
+            {o.xbest_bp_cnt, p + hi.plan_len + B + T + F, B}};
+        for (const Part &q : parts)
+            if (q.dst) std::memcpy(q.dst, q.src, 2 * (size_t)q.n);
+        o.cstar = st.cstar;
+        o.tmaxstar = st.tmaxstar;
+        o.iter = st.iter;
+    }
+    return BL_OK;
+}
+
+int bl_set_states(bl_handle *h, const bl_state *in)
+{
+    if (!h || !in) return BL_EINVAL;
+    if (h->failed) return BL_ESTATE;
+    for (int k = 0; k < h->n_inst; ++k) {
+        const bl_state &s = in[k];
+        if (!s.xold_bp_order || !s.xold_tour_cnt || !s.xold_field_order || !s.xold_bp_cnt || !s.xbest_bp_order ||
+            !s.xbest_tour_cnt || !s.xbest_field_order || !s.xbest_bp_cnt) {
+            h->err = "null plan array (instance " + std::to_string(k) + ")";
+            return BL_EINVAL;
+        }
+        const HostInst &hi = h->insts[(size_t)k];
+        if (check_plan(hi, s.xold_bp_order, s.xold_tour_cnt, s.xold_field_order, s.xold_bp_cnt) ||
+            check_plan(hi, s.xbest_bp_order, s.xbest_tour_cnt, s.xbest_field_order, s.xbest_bp_cnt)) {
+            h->err = "invalid plan encoding (instance " + std::to_string(k) + ")";
+            return BL_EINVAL;
+        }
+    }
+    std::vector<int32_t> offs;
+    const size_t bytes = states_layout(h, offs);
+    int rc = states_staging(h, bytes);
+    if (rc != BL_OK) return rc;
+    // the staging buffer may still feed an earlier copy on the stream
+    CK(h, cudaStreamSynchronize(h->stream));
+    std::memcpy(h->h_states, offs.data(), 4 * offs.size());
+    for (int k = 0; k < h->n_inst; ++k) {
+        const HostInst &hi = h->insts[(size_t)k];
+        const int B = hi.B, T = hi.T, F = hi.F;
+        int16_t *p = (int16_t *)(h->h_states + offs[(size_t)k]);
+        std::memset(p, 0, 4 * (size_t)hi.plan_len);
+        const bl_state &s = in[k];
+        struct Part { int16_t *dst; const int16_t *src; int n; } parts[8] = {
+            {p, s.xold_bp_order, B}, {p + B, s.xold_tour_cnt, T}, {p + B + T, s.xold_field_order, F},
+            {p + B + T + F, s.xold_bp_cnt, B}, {p + hi.plan_len, s.xbest_bp_order, B},
+            {p + hi.plan_len + B, s.xbest_tour_cnt, T}, {p + hi.plan_len + B + T, s.xbest_field_order, F},
+            {p + hi.plan_len + B + T + F, s.xbest_bp_cnt, B}};
+        for (const Part &q : parts) std::memcpy(q.dst, q.src, 2 * (size_t)q.n);
+        InstState st{};
+        st.cstar = s.cstar;
+        st.tmaxstar = s.tmaxstar;
+        st.iter = s.iter;
+        std::memcpy(p + 2 * hi.plan_len, &st, sizeof(st));
+    }
+    unsigned char *d = h->at<unsigned char>(h->ws.scratch);
+    CK(h, cudaMemcpyAsync(d, h->h_states, bytes, cudaMemcpyHostToDevice, h->stream));
+    CK(h, launch_state_pack(h->at<InstMeta>(h->ws.meta), h->n_inst, (const int32_t *)d, d, 1, h->stream));
+    return BL_OK;
+}
+
 int bl_search_score_slice(bl_handle *h, uint64_t *d_key)
 {
     if (!h || !d_key) return BL_EINVAL;
@@ -1187,6 +1303,7 @@ int bl_plan_free(bl_handle *h)
     if (!h) return BL_EINVAL;
     if (h->stream || h->base) cudaStreamSynchronize(h->stream);
     if (h->graph) cudaGraphExecDestroy(h->graph);
+    if (h->h_states) cudaFreeHost(h->h_states);
     if (h->capture_stream) cudaStreamDestroy(h->capture_stream);
     if (h->own_ws && h->base) cudaFree(h->base);
     if (h->l_feat) cudaFree(h->l_feat);

@@ -142,6 +142,8 @@ cudaError_t launch_decode(const LaunchCfg &cfg, const InstMeta *d_meta, int32_t 
                           cudaStream_t s);
 cudaError_t launch_apply_key(const LaunchCfg &cfg, const InstMeta *d_meta, SearchParams prm,
                              const unsigned long long *d_key, cudaStream_t s);
+cudaError_t launch_state_pack(const InstMeta *d_meta, int32_t n_inst, const int32_t *d_offs, unsigned char *d_buf,
+                              int32_t dir, cudaStream_t s);
 cudaError_t noalloc_scratch_address(void **ptr);
 cudaError_t launch_argmin_noalloc(const LaunchCfg &cfg, const InstMeta *d_meta, int32_t inst, int32_t use_best,
                                   uint32_t iter, float tmax_star, int32_t i0, int32_t n, SearchParams prm,

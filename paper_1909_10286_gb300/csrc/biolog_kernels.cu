@@ -1895,6 +1895,37 @@ __global__ void __launch_bounds__(SH::NT) apply_key_kernel(const InstMeta *__res
     }
 }
 
+// The search states of all instances to or from one packed buffer (one transfer each way for the
+// host): per instance, at byte offset offs[k], x_old and x* (plan_len int16 each) and the state record.
+// dir 0: device -> buffer, 1: buffer -> device (the state's work counter and error flag are cleared).
+__global__ void state_pack_kernel(const InstMeta *__restrict__ meta, const int32_t *__restrict__ offs,
+                                  unsigned char *__restrict__ buf, int32_t dir)
+{
+    const InstMeta &M = meta[blockIdx.x];
+    int16_t *p = (int16_t *)(buf + offs[blockIdx.x]);
+    InstState *st = (InstState *)(p + 2 * M.plan_len);
+    for (int k = threadIdx.x; k < M.plan_len; k += blockDim.x) {
+        if (dir == 0) { p[k] = M.xold[k]; p[M.plan_len + k] = M.xbest[k]; }
+        else { M.xold[k] = p[k]; M.xbest[k] = p[M.plan_len + k]; }
+    }
+    if (threadIdx.x == 0) {
+        if (dir == 0) *st = *M.state;
+        else {
+            InstState s = *st;
+            s.done = 0;
+            s.error = 0;
+            *M.state = s;
+        }
+    }
+}
+
+cudaError_t launch_state_pack(const InstMeta *d_meta, int32_t n_inst, const int32_t *d_offs, unsigned char *d_buf,
+                              int32_t dir, cudaStream_t s)
+{
+    state_pack_kernel<<<n_inst, 128, 0, s>>>(d_meta, d_offs, d_buf, dir);
+    return cudaGetLastError();
+}
+
 // ---------------------------------------------------------------------------
 // Cooperative scoring: L lanes per candidate, lane g holds tour g
 // ---------------------------------------------------------------------------
