@@ -326,6 +326,12 @@ def _equal_wall_time(inst, kw, net, pool, keep, rand_frac, iters):
 
 
 def run_learned(args, ws, rank, local):
+    line = measure_learned(args, args.workload, ws, rank, local)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
+def measure_learned(args, workload, ws, rank, local):
     """Configs 4 and 5: ranked proposals. value = exactly scored candidates/s; the
     roofline is the fused MLP forward's (the dominant kernel), timed on its own
     with CUDA events on the same pool of features."""
@@ -335,7 +341,7 @@ def run_learned(args, ws, rank, local):
     from paper_1909_10286_gb300 import biolog, learned
     from paper_1909_10286_gb300 import instances as I
 
-    spec = RANKED[args.workload]
+    spec = RANKED[workload]
     torch.cuda.set_device(local)
     pool, keep = spec["pool"], spec["keep"]
     rand_frac = spec["rand"] / (pool - keep)
@@ -410,7 +416,7 @@ def run_learned(args, ws, rank, local):
             "gpu_launches": args.steps * 5, "clocks": clk,
             "e2e": {"value": None, "note": "the end-to-end number is on the default paper line"},
             "roofline": {"bound": "tensor", "kernel": "fused_mlp_forward_kernel", "achieved": achieved, "peak": peak,
-                         "unit": "TFLOP/s", "frac": achieved / peak, "traffic": _traffic(args.workload),
+                         "unit": "TFLOP/s", "frac": achieved / peak, "traffic": _traffic(workload),
                          "ms_per_launch": ms_mlp,
                          "flop_per_launch": flop,
                          "peak_basis": "bf16_tflops (burst) of MEASURED_PEAKS.json; kernel timed alone"}}
@@ -419,8 +425,7 @@ def run_learned(args, ws, rank, local):
     if spec["compare_iters"] and rank == 0:
         line["equal_wall_time"] = _equal_wall_time(inst, kw, net0, pool, keep, rand_frac, spec["compare_iters"])
     net0.close()
-    if rank == 0:
-        print(json.dumps(line), flush=True)
+    return line
 
 
 def rank_instances(workload: str, seed: int, rank: int, n_inst: int):
@@ -516,6 +521,10 @@ def main():
                 sub = measure_plain(args, wl, ws, rank, local, args.cpu_budget / 2)
                 line[wl] = {k: sub[k] for k in ("value", "unit", "ms_per_step", "config", "gpu_launches", "clocks",
                                                 "e2e", "roofline", "cpu_baseline") if k in sub}
+            # ranked proposals on the paper-scale instance (the MLP's tensor-core roofline)
+            sub = measure_learned(args, "learned", ws, rank, local)
+            line["learned"] = {k: sub[k] for k in ("value", "unit", "ms_per_step", "config", "proposals_per_s",
+                                                   "gpu_launches", "clocks", "roofline") if k in sub}
         if ws == 1 and args.workload == "paper" and not args.no_time_to_target:
             from paper_1909_10286_gb300 import time_to_target
 

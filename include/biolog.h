@@ -312,6 +312,15 @@ int bl_mlp_grads(bl_mlp *m, const uint16_t *d_x, const float *d_target, int32_t 
 /* One Adam step (beta 0.9 / 0.999) with learning rate lr on that loss. */
 int bl_mlp_train_step(bl_mlp *m, const uint16_t *d_x, const float *d_target, int32_t M, float lr, float *h_loss);
 
+/* bl_mlp_train_step on a minibatch of `batch` rows (<= max_batch) drawn
+   uniformly with replacement from the n_rows rows of d_X [n_rows x in_dim]
+   (BF16) and d_T [n_rows], gathered in the library: row r of the minibatch of
+   Adam step t is floor(z n_rows / 2^64) with z = SplitMix64(seed + (t batch
+   + r) * 0x9E3779B97F4A7C15) (mod 2^64), so a run is reproducible from the
+   seed. */
+int bl_mlp_train_step_sampled(bl_mlp *m, const uint16_t *d_X, const float *d_T, int64_t n_rows, int32_t batch,
+                              uint64_t seed, float lr, float *h_loss);
+
 /* Copy parameters (which = 0) or the last gradients (which = 1) to host
    buffers: w1 [H x in], b1 [H], w2 [H x H], b2 [H], w3 [H x H], b3 [H],
    w4 [H], b4 [1]; NULL pointers are skipped. Synchronises. */

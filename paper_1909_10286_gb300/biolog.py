@@ -27,7 +27,8 @@ EXPORTS = ("bl_workspace_bytes", "bl_plan_init", "bl_plan_init_batch", "bl_searc
            "bl_get_config", "bl_plan_free", "bl_last_error", "bl_global_error", "bl_argmin_noalloc", "bl_wait_selftest",
            "bl_search_step_inspect", "bl_search_score_slice", "bl_search_apply", "bl_get_states", "bl_set_states",
            "bl_mlp_create", "bl_mlp_forward", "bl_mlp_grads", "bl_mlp_train_step", "bl_mlp_get", "bl_mlp_set",
-           "bl_mlp_free", "bl_mlp_last_error", "bl_gemm_bf16", "bl_features", "bl_search_step_learned")
+           "bl_mlp_free", "bl_mlp_last_error", "bl_gemm_bf16", "bl_features", "bl_search_step_learned",
+           "bl_mlp_train_step_sampled")
 
 
 class BiologError(RuntimeError):

@@ -827,6 +827,33 @@ __global__ void f32_to_bf16_kernel(const float *__restrict__ x, __nv_bfloat16 *_
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) y[i] = __float2bfloat16(x[i]);
 }
 
+// SplitMix64 (Steele, Lea, Flood, OOPSLA 2014): a counter-based 64-bit mix, here the row draw of a
+// training minibatch: row r of step t reads mix(seed + (t * batch + r) * golden) -> uniform below n.
+__device__ __forceinline__ unsigned long long splitmix64(unsigned long long z)
+{
+    z += 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+// Gather a minibatch of `batch` rows drawn uniformly with replacement from n rows of X [n x in] (BF16)
+// and T [n] into xb [batch x in] and tb [batch].
+__global__ void sample_rows_kernel(const __nv_bfloat16 *__restrict__ X, const float *__restrict__ T, long long n,
+                                   int in, int batch, unsigned long long seed, unsigned long long step,
+                                   __nv_bfloat16 *__restrict__ xb, float *__restrict__ tb)
+{
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < (long long)batch * in;
+         e += (long long)gridDim.x * blockDim.x) {
+        const int r = (int)(e / in), k = (int)(e % in);
+        const unsigned long long z = splitmix64(seed + (step * (unsigned long long)batch + (unsigned long long)r) *
+                                                           0x9E3779B97F4A7C15ull);
+        const long long row = (long long)__umul64hi(z, (unsigned long long)n);   // floor(z n / 2^64)
+        xb[e] = X[row * in + k];
+        if (k == 0) tb[r] = T[row];
+    }
+}
+
 }  // namespace mlp
 
 // at least 80 KB, so no more than two CTAs (2 x 256 TMEM columns) are resident on one SM
@@ -964,6 +991,14 @@ cudaError_t launch_adam(float *w, void *wb, const float *g, float *m, float *v, 
     for (int i = 0; i < step; ++i) { c1 *= b1; c2 *= b2; }
     mlp::adam_kernel<<<256, 256, 0, s>>>(w, reinterpret_cast<__nv_bfloat16 *>(wb), g, m, v, n, lr, b1, b2, eps,
                                          1.f - c1, 1.f - c2);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_sample_rows(const void *X, const float *T, long long n, int in, int batch, unsigned long long seed,
+                               unsigned long long step, void *xb, float *tb, cudaStream_t s)
+{
+    mlp::sample_rows_kernel<<<592, 256, 0, s>>>(reinterpret_cast<const __nv_bfloat16 *>(X), T, n, in, batch, seed,
+                                                step, reinterpret_cast<__nv_bfloat16 *>(xb), tb);
     return cudaGetLastError();
 }
 

@@ -27,6 +27,8 @@ cudaError_t launch_colsum(const void *x, float *out, int M, int H, cudaStream_t 
 cudaError_t launch_adam(float *w, void *wb, const float *g, float *m, float *v, int n, float lr, float b1, float b2,
                         float eps, int step, cudaStream_t s);
 cudaError_t launch_f32_to_bf16(const float *x, void *y, int n, cudaStream_t s);
+cudaError_t launch_sample_rows(const void *X, const float *T, long long n, int in, int batch, unsigned long long seed,
+                               unsigned long long step, void *xb, float *tb, cudaStream_t s);
 int fused_mlp_nbuf(int I, int H);
 size_t fused_mlp_pack_bytes(int I, int H);
 cudaError_t launch_fused_pack(const void *w1, const void *w2, const void *w3, int I, int H, void *out, cudaStream_t s);
@@ -66,6 +68,8 @@ struct bl_mlp {
     void *wpack = nullptr;
     bool packed = false;
     int fused_nbuf = 0;
+    uint16_t *xs = nullptr;   // sampled minibatch (bl_mlp_train_step_sampled), max_batch rows
+    float *ts = nullptr;
     std::vector<void *> allocs;
     std::string msg;
     int lin(int l) const { return l == 0 ? in : H; }
@@ -311,6 +315,19 @@ int bl_mlp_train_step(bl_mlp *m, const uint16_t *d_x, const float *d_target, int
     MK(m, launch_adam(m->b4, nullptr, m->gb4, m->mb4, m->vb4, 1, lr, b1, b2, eps, m->step, m->stream));
     m->packed = false;
     return BL_OK;
+}
+
+int bl_mlp_train_step_sampled(bl_mlp *m, const uint16_t *d_X, const float *d_T, int64_t n_rows, int32_t batch,
+                              uint64_t seed, float lr, float *h_loss)
+{
+    if (!m || !d_X || !d_T || n_rows < 1 || batch < 1 || batch > m->max_batch) return BL_EINVAL;
+    if (!m->xs) {
+        MK(m, dalloc(m, &m->xs, (size_t)m->max_batch * m->in));
+        MK(m, dalloc(m, &m->ts, (size_t)m->max_batch));
+    }
+    MK(m, launch_sample_rows(d_X, d_T, n_rows, m->in, batch, seed, (unsigned long long)m->step, m->xs, m->ts,
+                             m->stream));
+    return bl_mlp_train_step(m, m->xs, m->ts, batch, lr, h_loss);
 }
 
 // Parameters and gradients in host buffers, layer by layer: w1 [H x in], b1 [H],

@@ -56,18 +56,13 @@ def collect(instances, iters: int, sample: int, seed: int = 100, n_cand: int | N
 def train(X, T, hidden: int = 256, steps: int = 2000, batch: int = 4096, lr: float = 1e-3, seed: int = 0,
           stream=None, max_batch: int = 1 << 18, log_every: int = 0):
     """Adam on mean squared error over random minibatches; returns (MLP, losses)."""
-    import torch
-
     net = MLP(NFEAT, hidden, max_batch=max(batch, max_batch), seed=seed, stream=stream)
-    g = torch.Generator(device="cuda")
-    g.manual_seed(seed)
     losses = []
-    n = X.shape[0]
+    X, T = X.contiguous(), T.contiguous()
     for s in range(steps):
-        idx = torch.randint(0, n, (batch,), device="cuda", generator=g)
-        xb, tb = X[idx].contiguous(), T[idx].contiguous()
         rate = lr * (0.1 ** (s / max(steps, 1)))   # geometric decay to lr/10
-        losses.append(net.train_step(xb, tb, rate))
+        # the library draws the minibatch (uniform rows, with replacement) and takes the Adam step
+        losses.append(net.train_step_sampled(X, T, batch, seed, rate))
         if log_every and s % log_every == 0:
             print(f"step {s}: loss {losses[-1]:.4f}")
     return net, losses

@@ -18,6 +18,7 @@ def _lib():
         L.bl_mlp_forward.argtypes = [vp, vp, C.c_int32, vp]
         L.bl_mlp_grads.argtypes = [vp, vp, vp, C.c_int32, vp]
         L.bl_mlp_train_step.argtypes = [vp, vp, vp, C.c_int32, C.c_float, vp]
+        L.bl_mlp_train_step_sampled.argtypes = [vp, vp, vp, C.c_int64, C.c_int32, C.c_uint64, C.c_float, vp]
         L.bl_mlp_get.argtypes = [vp, C.c_int32, vp, vp, vp, vp, vp, vp, vp, vp]
         L.bl_mlp_set.argtypes = [vp, vp, vp, vp, vp, vp, vp, vp, vp]
         L.bl_mlp_free.argtypes = [vp]
@@ -107,6 +108,13 @@ class MLP:
     def train_step(self, x, target, lr: float) -> float:
         loss = C.c_float(0.0)
         _check(_lib().bl_mlp_train_step(self.h, _ptr(x), _ptr(target), x.shape[0], float(lr), C.byref(loss)), self.h)
+        return loss.value
+
+    def train_step_sampled(self, X, T, batch: int, seed: int, lr: float) -> float:
+        """One Adam step on `batch` rows the library draws from the dataset (X [n x in] bf16, T [n] float32)."""
+        loss = C.c_float(0.0)
+        _check(_lib().bl_mlp_train_step_sampled(self.h, _ptr(X), _ptr(T), int(X.shape[0]), int(batch), int(seed),
+                                                float(lr), C.byref(loss)), self.h)
         return loss.value
 
     def close(self):

@@ -176,3 +176,39 @@ def test_inference_after_training_step_uses_updated_weights():
     assert not np.allclose(y0, y1)
     _check_rows(y1, ref, x.float().cpu().numpy())
     net.close()
+
+
+def _splitmix64(z):
+    m = (1 << 64) - 1
+    z = (z + 0x9E3779B97F4A7C15) & m
+    z = ((z ^ (z >> 30)) * 0xBF58476D1CE4E5B9) & m
+    z = ((z ^ (z >> 27)) * 0x94D049BB133111EB) & m
+    return z ^ (z >> 31)
+
+
+def test_sampled_train_step_draws_the_documented_rows():
+    """bl_mlp_train_step_sampled equals bl_mlp_train_step on the rows its documented SplitMix64 draw
+    selects (computed here in Python), bit for bit, over two Adam steps; and the same seed repeats."""
+    from paper_1909_10286_gb300 import mlp
+    import torch
+
+    rng = np.random.default_rng(4)
+    n, I, H, batch, seed = 5003, 64, 64, 256, 12345
+    X = _bf16_tensor(rng.standard_normal((n, I)))
+    T = torch.tensor(rng.standard_normal(n), dtype=torch.float32).cuda()
+    a = mlp.MLP(I, H, max_batch=batch, seed=7)
+    b = mlp.MLP(I, H, max_batch=batch, seed=7)
+    c = mlp.MLP(I, H, max_batch=batch, seed=7)
+    for step in range(2):
+        rows = [(_splitmix64((seed + ((step * batch + r) * 0x9E3779B97F4A7C15)) & ((1 << 64) - 1)) * n) >> 64
+                for r in range(batch)]
+        idx = torch.tensor(rows, dtype=torch.int64, device="cuda")
+        la = a.train_step_sampled(X, T, batch, seed, 1e-3)
+        lb = b.train_step(X[idx].contiguous(), T[idx].contiguous(), 1e-3)
+        lc = c.train_step_sampled(X, T, batch, seed, 1e-3)
+        # the loss is summed with atomics (order-dependent in the last bits); the weights are exact
+        assert la == pytest.approx(lb, rel=1e-6) and lc == pytest.approx(la, rel=1e-6)
+    for pa, pb, pc in zip(a.get(), b.get(), c.get()):
+        assert np.array_equal(pa, pb) and np.array_equal(pa, pc)
+    for net in (a, b, c):
+        net.close()
