@@ -252,24 +252,37 @@ gemm_bf16_tn_kernel(const __nv_bfloat16 *__restrict__ A, const __nv_bfloat16 *__
 // ---- fused inference: all three layers and the head per 128-row tile ------
 //
 // y = w4 . relu(W3 relu(W2 relu(W1 x + b1) + b2) + b3) + b4 for M rows, one
-// persistent CTA per SM looping over 128-row tiles. The accumulator of the
-// layer in flight is 128 TMEM lanes x H FP32 columns; the hidden activations
-// never leave shared memory: each layer's epilogue (bias, ReLU, BF16 rounding
-// -- the same rounding the layer-by-layer path stores) writes them straight
-// into the A-operand layout of the next layer. The weights of the three
-// layers are pre-packed (fused_pack_kernel) into K chunks of 64 in the
-// B-operand layout, so each chunk is one bulk copy into a ring of NBUF
-// shared buffers, loaded ahead while the tensor cores work on earlier chunks.
+// persistent CTA per SM looping over pairs of 128-row tiles (A and B). The
+// accumulator of a tile's layer in flight is 128 TMEM lanes x H FP32 columns;
+// the hidden activations never leave shared memory: each layer's epilogue
+// (bias, ReLU, BF16 rounding -- the same rounding the layer-by-layer path
+// stores) writes them straight into the A-operand layout of the tile's next
+// layer. The weights of the three layers are pre-packed (fused_pack_kernel)
+// into K chunks of 64 in the B-operand layout, so each chunk is one bulk copy
+// into a ring of NBUF shared buffers, loaded ahead while the tensor cores work
+// on earlier chunks.
 //
 // Shared layouts (no swizzle, K-major, 8x8 core matrices of 16-byte rows):
 //   activations X (tile of the input) and Hs (hidden): core matrix (row group
 //   rg, k block kb) at kb * 2048 + rg * 128 bytes   -> LBO 2048, SBO 128
 //   weight chunk: core matrix (n group ng, k block kb) at kb * (H * 16) + ng * 128
 //                                                      -> LBO H * 16, SBO 128
-// Epilogue: warp w (16 warps) reads TMEM lanes 32 (w % 4) .. +31 of tile
-// (w / 4) % 2, columns of half w / 8; four warps per scheduler hide the
-// latency of the TMEM loads and shared stores of one another.
-constexpr int FTHREADS = 512;
+// Roles (18 warps). The two tiles run a layer apart: while the tensor cores
+// work on one tile's layer, the other tile's epilogue runs.
+//   warps 0-7 / 8-15: the epilogue group of tile A / B. Warp w of a group reads
+//     TMEM lanes 32 (w % 4) .. +31 of its tile's accumulator, column half
+//     (w / 4) % 2; the group stages its tile's input rows too.
+//   warp 16, lane 0: issues each layer's MMAs tile by tile (A, then B) as soon
+//     as the tile's operand is written and the chunk's weights have landed, and
+//     never waits for the tensor cores.
+//   warp 17, lane 0: refills the weight ring in the issuer's order (per pair:
+//     layer, tile, chunk -- each tile's layer streams its weights again): waits
+//     until a slot's MMAs are done and copies the next chunk into it.
+// The issuer and the producer are alone in their warps: lanes of one warp that
+// wait on different barriers would take turns.
+constexpr int FGROUP = 256;                // threads of one epilogue group
+constexpr int FEPI = 2 * FGROUP;           // epilogue threads
+constexpr int FTHREADS = FEPI + 64;   // + the issuer warp and the producer warp
 constexpr int FKMAX = 64;   // largest K per weight chunk
 
 // Weight chunking: a bulk copy costs about the same time whatever its size up
@@ -337,42 +350,17 @@ __device__ __forceinline__ void tc_mma(uint32_t tmem, uint64_t ad, uint64_t bd, 
         : "memory");
 }
 
+// 16 accumulator columns of this warp's 32 TMEM lanes; the load and its wait are one asm statement, so
+// the registers cannot be read before they have landed
 __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t *v)
 {
     asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];\n\t"
+        "tcgen05.wait::ld.sync.aligned;"
         : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]), "=r"(v[8]),
           "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
-        : "r"(taddr));
-    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-}
-
-// tcgen05.ld without the wait, and a pin that keeps the loaded registers from
-// being read before the wait (the empty asm "redefines" them after it)
-__device__ __forceinline__ void tmem_ld16_nowait(uint32_t taddr, uint32_t *v)
-{
-    asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-        : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]), "=r"(v[8]),
-          "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
-        : "r"(taddr));
-}
-__device__ __forceinline__ void pin16(uint32_t *v)
-{
-    asm volatile("" : "+r"(v[0]), "+r"(v[1]), "+r"(v[2]), "+r"(v[3]), "+r"(v[4]), "+r"(v[5]), "+r"(v[6]), "+r"(v[7]),
-                 "+r"(v[8]), "+r"(v[9]), "+r"(v[10]), "+r"(v[11]), "+r"(v[12]), "+r"(v[13]), "+r"(v[14]), "+r"(v[15]));
-}
-// 16 * nb accumulator columns from c0 (nb <= NB) with a single wait
-template <int NB>
-__device__ __forceinline__ void tmem_ld_group(uint32_t taddr, int nb, uint32_t (*v)[16])
-{
-#pragma unroll
-    for (int b = 0; b < NB; ++b)
-        if (b < nb) tmem_ld16_nowait(taddr + 16u * b, v[b]);
-    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-    for (int b = 0; b < NB; ++b)
-        if (b < nb) pin16(v[b]);
+        : "r"(taddr)
+        : "memory");
 }
 
 // Pack W (layer l: [H x K_l] row-major BF16) into the chunked B-operand layout.
@@ -445,6 +433,30 @@ __device__ __forceinline__ void fused_stage_x(unsigned char *xs, const __nv_bflo
     }
 }
 
+// Named barrier `id` over the 256 threads of one epilogue group; returns the AND of `v` over them
+__device__ __forceinline__ bool group_and(int id, bool v)
+{
+    uint32_t r;
+    asm volatile(
+        "{\n\t.reg .pred p, q;\n\t"
+        "setp.ne.u32 p, %1, 0;\n\t"
+        "bar.red.and.pred q, %2, %3, p;\n\t"
+        "selp.u32 %0, 1, 0, q;\n\t}"
+        : "=r"(r)
+        : "r"((uint32_t)v), "r"(id), "r"(FGROUP)
+        : "memory");
+    return r != 0;
+}
+__device__ __forceinline__ void group_sync(int id)
+{
+    asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(FGROUP) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+// 18 warps: a sub-partition holds five of them, which caps a thread at 96 registers
 __global__ void __launch_bounds__(FTHREADS, 1)
 fused_mlp_forward_kernel(const __nv_bfloat16 *__restrict__ X, int M, int I, int H, const uint4 *__restrict__ wpack,
                          const float *__restrict__ b1, const float *__restrict__ b2, const float *__restrict__ b3,
@@ -452,15 +464,16 @@ fused_mlp_forward_kernel(const __nv_bfloat16 *__restrict__ X, int M, int I, int 
                          unsigned int *__restrict__ err)
 {
     extern __shared__ __align__(1024) unsigned char smem[];
-    __shared__ uint64_t tma_bar[4], mma_bar[4], layer_bar, drain_bar;
+    // tma_bar[s]: slot s's weights landed; mma_bar[s]: slot s's MMAs done;
+    // acc_bar[t]: tile t's layer done; act_bar[t]: tile t's operand for its next layer written (FGROUP arrivals)
+    __shared__ uint64_t tma_bar[4], mma_bar[4], acc_bar[2], act_bar[2], drain_bar;
     __shared__ uint32_t tmem_base_sh;
     __shared__ int fail_sh;
+    __shared__ unsigned long long loaded_sh;   // chunk copies the producer issued (for the drain)
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const FusedGeom G = fused_geom(I, H);
     const int nch1 = G.nch1, nch2 = G.nch2, cpt = G.cpt;
     const FusedSmem L = fused_smem(I, H, nbuf);
-    // the two tiles' activation buffers: act_of(t) (no pointer array: it would live in local memory)
-    auto act_of = [&](int t) { return smem + (t ? L.act1 : L.act0); };
     unsigned char *wb = smem + L.wb;
     float *par = reinterpret_cast<float *>(smem + L.par);   // b1 | b2 | b3 | w4 | b4
     for (int i = tid; i < H; i += FTHREADS) {
@@ -471,7 +484,6 @@ fused_mlp_forward_kernel(const __nv_bfloat16 *__restrict__ X, int M, int I, int 
     const int ntiles = (M + 127) / 128;
     const int npairs = (ntiles + 1) / 2;
     const int my_pairs = blockIdx.x < npairs ? (npairs - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
-    const long long total = (long long)my_pairs * cpt;   // weight chunks this CTA consumes
 
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base_sh)),
@@ -484,226 +496,216 @@ fused_mlp_forward_kernel(const __nv_bfloat16 *__restrict__ X, int M, int I, int 
             asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&tma_bar[b])) : "memory");
             asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&mma_bar[b])) : "memory");
         }
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&layer_bar)) : "memory");
+        for (int t = 0; t < 2; ++t) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&acc_bar[t])) : "memory");
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&act_bar[t])), "r"(FGROUP) : "memory");
+        }
         asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&drain_bar)) : "memory");
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         fail_sh = 0;
+        loaded_sh = 0ull;
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const uint32_t tmem = tmem_base_sh;   // tile A's accumulator at column 0, tile B's at column 256
-    const uint32_t idesc = instr_desc(128, H);
+    auto failed = [&]() { return (volatile int &)fail_sh != 0; };
 
-    // producer state (thread 0): chunks are loaded nbuf ahead; each barrier's
-    // completions are waited on in order, so one parity bit per barrier suffices.
-    // Ring slots and chunk numbers advance by counters (no 64-bit division between MMAs).
-    long long loaded = 0;        // chunks whose bulk copy was issued
+    // the issuer's state, kept for the drain
     long long consumed = 0;      // chunks whose MMAs were issued
-    int lb = 0, lj = 0;          // ring slot and chunk-in-pair of the next load
-    int cb = 0, cj = 0;          // ring slot and chunk-in-pair of the next chunk to consume
-    uint32_t tma_ph = 0, mma_ph = 0;   // bit b: parity of the next wait on buffer b
-    // descriptors: the start-address field (bits 0-13, address >> 4) is added per operand
-    const uint64_t a_tmpl = smem_desc(smem, 2048, 128) & ~0x3FFFull;
-    const uint64_t b_tmpl = smem_desc(smem, (uint32_t)H * 16, 128) & ~0x3FFFull;
-    const uint32_t a_addr0 = smem_u32(smem + L.act0) >> 4, a_addr1 = smem_u32(smem + L.act1) >> 4;
-    const uint32_t w_addr = smem_u32(wb) >> 4;
-    auto load_chunk = [&]() {
-        int layer, c, kc;
-        size_t off;
-        fused_chunk(G, H, lj, layer, c, kc, off);
-        const uint32_t bytes = (uint32_t)H * kc * 2;
-        mbar_expect_tx_bytes(&tma_bar[lb], bytes);
-        bulk_g2s(wb + (size_t)lb * buf_bytes, wpack + off / 16, bytes, &tma_bar[lb]);
-        ++loaded;
-        lb = lb + 1 == nbuf ? 0 : lb + 1;
-        lj = lj + 1 == cpt ? 0 : lj + 1;
-    };
-    // issue the MMAs of the next chunk for both tiles; false if a bounded wait gave up
-    auto consume_chunk = [&]() -> bool {
-        const int b = cb;
-        if (!mbar_wait(&tma_bar[b], (tma_ph >> b) & 1u)) return false;
-        tma_ph ^= 1u << b;
-        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        int layer, c, kc;
-        size_t off;
-        fused_chunk(G, H, cj, layer, c, kc, off);
-        const int K = layer == 0 ? I : H;
-        const uint32_t bsl = w_addr + (uint32_t)(b * (buf_bytes >> 4));
-        const int ns = (min(kc, K - c * kc) + 15) / 16;   // K steps of 16 in this chunk (zero padded past K)
-        for (int s = 0; s < ns; ++s) {
-            const int k = c * kc + s * 16;
-            const uint64_t bd = b_tmpl | (uint64_t)(bsl + (uint32_t)(2 * s * H));   // (2 s H 16) >> 4
-            const uint32_t ko = (uint32_t)(k / 8) * (2048 >> 4);
-            const uint32_t acc = (c > 0 || s > 0) ? 1u : 0u;
-            tc_mma(tmem, a_tmpl | (uint64_t)(a_addr0 + ko), bd, idesc, acc);
-            tc_mma(tmem + (uint32_t)TMEM_COLS, a_tmpl | (uint64_t)(a_addr1 + ko), bd, idesc, acc);
-        }
-        tc_commit(&mma_bar[b]);
-        const int pb = b == 0 ? nbuf - 1 : b - 1;   // the slot of chunk consumed - 1
-        ++consumed;
-        cb = cb + 1 == nbuf ? 0 : cb + 1;
-        cj = cj + 1 == cpt ? 0 : cj + 1;
-        // the buffer of the previous chunk is free once its MMAs are done: load the chunk nbuf ahead
-        // into it (unless the end of the previous layer already did, see refill_early)
-        if (consumed >= 2 && loaded < total && loaded == consumed - 2 + nbuf) {
-            if (!mbar_wait(&mma_bar[pb], (mma_ph >> pb) & 1u)) return false;
-            mma_ph ^= 1u << pb;
-            load_chunk();
-        }
-        return true;
-    };
-    // after a layer's last chunk: once its MMAs are done (the layer is), its buffer takes the chunk
-    // nbuf ahead, so that this copy runs during the epilogue instead of at the next layer's start
-    auto refill_early = [&]() -> bool {
-        if (loaded < total && loaded == consumed - 1 + nbuf) {
-            const int sl = cb == 0 ? nbuf - 1 : cb - 1;   // the buffer of chunk consumed - 1
-            if (!mbar_wait(&mma_bar[sl], (mma_ph >> sl) & 1u)) return false;
-            mma_ph ^= 1u << sl;
-            load_chunk();
-        }
-        return true;
-    };
+    uint32_t tma_ph = 0;         // bit b: parity of the next wait on tma_bar[b]
 
-    if (tid == 0)
-        while (loaded < total && loaded < nbuf) load_chunk();
-    // epilogue roles: warp w reads TMEM lanes 32 (w % 4) .. +31 of tile (w / 4) % 2, column half w / 8
-    const int q = warp & 3, t_ep = (warp >> 2) & 1, half = warp >> 3;
-    const int row_in_tile = 32 * q + lane;
-    const int col_lo = half * (H / 2), col_hi = col_lo + H / 2;   // H / 2 is a multiple of 16
-    // The next pair's inputs are loaded into registers while the last layer's MMAs run
-    // (16-byte rows, at most XPRE segments per thread); other widths are staged directly.
-    constexpr int XPRE = 4;
-    const int xsegs = 128 * G.xkb;   // 16-byte segments per tile
-    const bool xpre = (I % 8) == 0 && (reinterpret_cast<uintptr_t>(X) & 15) == 0 && 2 * xsegs <= XPRE * FTHREADS;
-    uint4 xr[XPRE];
-    auto x_load = [&](int pair) {
-#pragma unroll
-        for (int k = 0; k < XPRE; ++k) {
-            const int s = tid + k * FTHREADS, t = s >= xsegs ? 1 : 0, s2 = s - t * xsegs;
-            const int row = (2 * pair + t) * 128 + (s2 & 127), kk = (s2 >> 7) * 8;
-            xr[k] = (s < 2 * xsegs && row < M && kk < I) ? __ldg(reinterpret_cast<const uint4 *>(X + (size_t)row * I + kk))
-                                                       : make_uint4(0u, 0u, 0u, 0u);
+    if (warp == FEPI / 32) {
+        if (lane == 0) {
+            // ---- MMA issuer: per pair, layer by layer, tile A then tile B ----
+            const uint32_t idesc = instr_desc(128, H);
+            // descriptors: the start-address field (bits 0-13, address >> 4) is added per operand
+            const uint64_t a_tmpl = smem_desc(smem, 2048, 128) & ~0x3FFFull;
+            const uint64_t b_tmpl = smem_desc(smem, (uint32_t)H * 16, 128) & ~0x3FFFull;
+            const uint32_t a_addr0 = smem_u32(smem + L.act0) >> 4, a_addr1 = smem_u32(smem + L.act1) >> 4;
+            const uint32_t w_addr = smem_u32(wb) >> 4;
+            uint32_t act_ph = 0;   // bit t: parity of the next wait on act_bar[t]
+            int cb = 0;            // ring slot of the next chunk
+            bool good = true;
+            for (int p = 0; p < my_pairs && good; ++p)
+                for (int layer = 0; layer < 3 && good; ++layer) {
+                    const int nch = layer == 0 ? nch1 : nch2, jj0 = layer == 0 ? 0 : (layer == 1 ? nch1 : nch1 + nch2);
+                    for (int t = 0; t < 2 && good; ++t) {
+                        // tile t's operand (its input, or the previous layer's epilogue) is in place, and that
+                        // epilogue has read its accumulator
+                        if (failed() || !mbar_wait(&act_bar[t], (act_ph >> t) & 1u)) { good = false; break; }
+                        act_ph ^= 1u << t;
+                        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                        const uint32_t a_addr = t ? a_addr1 : a_addr0, acc_t = tmem + (uint32_t)(t * TMEM_COLS);
+                        for (int c = 0; c < nch; ++c) {
+                            if (!mbar_wait(&tma_bar[cb], (tma_ph >> cb) & 1u)) { good = false; break; }
+                            tma_ph ^= 1u << cb;
+                            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                            int lay, cc, kc;
+                            size_t off;
+                            fused_chunk(G, H, jj0 + c, lay, cc, kc, off);
+                            const int K = lay == 0 ? I : H;
+                            const uint32_t bsl = w_addr + (uint32_t)(cb * (buf_bytes >> 4));
+                            const int ns = (min(kc, K - cc * kc) + 15) / 16;   // K steps of 16 (zero padded past K)
+                            for (int s = 0; s < ns; ++s) {
+                                const int k = cc * kc + s * 16;
+                                const uint64_t bd = b_tmpl | (uint64_t)(bsl + (uint32_t)(2 * s * H));   // (2 s H 16) >> 4
+                                const uint32_t ko = (uint32_t)(k / 8) * (2048 >> 4);
+                                tc_mma(acc_t, a_tmpl | (uint64_t)(a_addr + ko), bd, idesc, (cc > 0 || s > 0) ? 1u : 0u);
+                            }
+                            tc_commit(&mma_bar[cb]);
+                            ++consumed;
+                            cb = cb + 1 == nbuf ? 0 : cb + 1;
+                        }
+                        if (good) tc_commit(&acc_bar[t]);
+                    }
+                }
+            if (!good) fail_sh = 1;
         }
-    };
-    auto x_store = [&]() {
-#pragma unroll
-        for (int k = 0; k < XPRE; ++k) {
-            const int s = tid + k * FTHREADS, t = s >= xsegs ? 1 : 0, s2 = s - t * xsegs;
-            const int r = s2 & 127;
-            if (s < 2 * xsegs)
-                *reinterpret_cast<uint4 *>(act_of(t) + (s2 >> 7) * 2048 + (r >> 3) * 128 + (r & 7) * 16) = xr[k];
-        }
-    };
-    uint32_t layer_ph = 0;
-    bool ok = true;
-    for (int p = 0; p < my_pairs && ok; ++p) {
-        const int pair = (int)blockIdx.x + p * (int)gridDim.x;
-        // both tiles' inputs into their activation buffers (the last layer's MMAs of the
-        // previous pair, the readers of these buffers, completed before its epilogue)
-        if (xpre && p > 0) {
-            x_store();
-        } else {
-            fused_stage_x(act_of(0), X, M, I, G.xkb, (2 * pair) * 128, tid, FTHREADS);
-            fused_stage_x(act_of(1), X, M, I, G.xkb, (2 * pair + 1) * 128, tid, FTHREADS);
-        }
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        __syncthreads();
-        for (int layer = 0; layer < 3 && ok; ++layer) {
-            const int nchunks = layer == 0 ? nch1 : nch2;
-            if (tid == 0) {
-                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-                bool good = true;
-                for (int c = 0; c < nchunks && good; ++c) good = consume_chunk();
-                if (good) tc_commit(&layer_bar);
-                if (good) good = refill_early();
-                if (!good) fail_sh = 1;
+        __syncwarp();
+    } else if (warp == FEPI / 32 + 1) {
+        if (lane == 0) {
+            // ---- weight producer: the chunks in the issuer's order (per pair: layer, tile, chunk) ----
+            const long long total = (long long)my_pairs * 2 * cpt;
+            long long loaded = 0;
+            uint32_t mma_ph = 0;   // bit b: parity of the next wait on mma_bar[b]
+            int lb = 0, layer = 0, t = 0, c = 0;
+            for (; loaded < total; ++loaded) {
+                // slot lb's previous chunk (loaded - nbuf) must be consumed first
+                if (loaded >= nbuf) {
+                    if (failed() || !mbar_wait(&mma_bar[lb], (mma_ph >> lb) & 1u)) { fail_sh = 1; break; }
+                    mma_ph ^= 1u << lb;
+                }
+                int lay, cc, kc;
+                size_t off;
+                fused_chunk(G, H, (layer == 0 ? 0 : (layer == 1 ? nch1 : nch1 + nch2)) + c, lay, cc, kc, off);
+                const uint32_t bytes = (uint32_t)H * kc * 2;
+                mbar_expect_tx_bytes(&tma_bar[lb], bytes);
+                bulk_g2s(wb + (size_t)lb * buf_bytes, wpack + off / 16, bytes, &tma_bar[lb]);
+                lb = lb + 1 == nbuf ? 0 : lb + 1;
+                if (++c == (layer == 0 ? nch1 : nch2)) {
+                    c = 0;
+                    if (++t == 2) { t = 0; layer = layer == 2 ? 0 : layer + 1; }
+                }
             }
-            if (layer == 2 && xpre && p + 1 < my_pairs) x_load(pair + (int)gridDim.x);
-            __syncwarp();
-            const bool got = (volatile int &)fail_sh == 0 && mbar_wait(&layer_bar, layer_ph);
-            layer_ph ^= 1u;
-            ok = __syncthreads_and(got ? 1 : 0) != 0;
-            if (!ok) break;
-            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            const uint32_t taddr = tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(t_ep * TMEM_COLS);
-            const float *bias = par + layer * H;
-            if (layer < 2) {
-                unsigned char *dst0 = act_of(t_ep) + (row_in_tile >> 3) * 128 + (row_in_tile & 7) * 16;
-                for (int c0 = col_lo; c0 < col_hi; c0 += 32) {
-                    const int nb = min(2, (col_hi - c0) / 16);
-                    uint32_t v[2][16];
-                    tmem_ld_group<2>(taddr + (uint32_t)c0, nb, v);
+            loaded_sh = (unsigned long long)loaded;
+        }
+        __syncwarp();
+    } else {
+        // ---- epilogue group t (warps 8 t .. 8 t + 7): tile t of every pair ----
+        const int t = warp >> 3, gw = warp & 7, gtid = tid & (FGROUP - 1), bar_id = 1 + t;
+        const int q = gw & 3, half = gw >> 2;   // TMEM lanes 32 q .. 32 q + 31, column half
+        const int row_in_tile = 32 * q + lane;
+        const int col_lo = half * (H / 2), col_hi = col_lo + H / 2;   // H / 2 is a multiple of 16
+        unsigned char *act = smem + (t ? L.act1 : L.act0);
+        const uint32_t taddr = tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(t * TMEM_COLS);
+        // The next pair's input rows are loaded into registers while this tile's last layer runs
+        // (16-byte rows, at most XPRE segments per thread); other widths are staged directly.
+        constexpr int XPRE = 4;
+        const int xsegs = 128 * G.xkb;   // 16-byte segments per tile
+        const bool xpre = (I % 8) == 0 && (reinterpret_cast<uintptr_t>(X) & 15) == 0 && xsegs <= XPRE * FGROUP;
+        uint4 xr[XPRE];
+        auto x_load = [&](int tile) {
 #pragma unroll
-                    for (int b = 0; b < 2; ++b) {
-                        if (b >= nb) break;
-                        const int cb = c0 + 16 * b;
+            for (int k = 0; k < XPRE; ++k) {
+                const int s = gtid + k * FGROUP;
+                const int row = tile * 128 + (s & 127), kk = (s >> 7) * 8;
+                xr[k] = (s < xsegs && row < M && kk < I) ? __ldg(reinterpret_cast<const uint4 *>(X + (size_t)row * I + kk))
+                                                        : make_uint4(0u, 0u, 0u, 0u);
+            }
+        };
+        auto x_store = [&]() {
+#pragma unroll
+            for (int k = 0; k < XPRE; ++k) {
+                const int s = gtid + k * FGROUP, r = s & 127;
+                if (s < xsegs) *reinterpret_cast<uint4 *>(act + (s >> 7) * 2048 + (r >> 3) * 128 + (r & 7) * 16) = xr[k];
+            }
+        };
+        uint32_t acc_ph = 0;
+        bool gok = true;   // uniform over the group (every decision below is voted on)
+        for (int p = 0; p < my_pairs && gok; ++p) {
+            const int pair = (int)blockIdx.x + p * (int)gridDim.x, tile = 2 * pair + t;
+            if (xpre && p > 0) x_store();
+            else fused_stage_x(act, X, M, I, G.xkb, tile * 128, gtid, FGROUP);
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            mbar_arrive(&act_bar[t]);
+            for (int layer = 0; layer < 3; ++layer) {
+                if (layer == 2 && xpre && p + 1 < my_pairs) x_load(tile + 2 * (int)gridDim.x);
+                const bool got = !failed() && mbar_wait(&acc_bar[t], acc_ph);
+                acc_ph ^= 1u;
+                gok = group_and(bar_id, got);
+                if (!gok) break;
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                const float *bias = par + layer * H;
+                if (layer < 2) {
+                    unsigned char *dst0 = act + (row_in_tile >> 3) * 128 + (row_in_tile & 7) * 16;
+                    for (int cb = col_lo; cb < col_hi; cb += 16) {   // 16 columns per TMEM load (96 registers)
+                        uint32_t v[16];
+                        tmem_ld16(taddr + (uint32_t)cb, v);
                         const float4 *b4v = reinterpret_cast<const float4 *>(bias + cb);
                         uint32_t w[8];
 #pragma unroll
                         for (int qq = 0; qq < 4; ++qq) {
                             const float4 bb = b4v[qq];
-                            w[2 * qq] = relu_bf16x2(__uint_as_float(v[b][4 * qq]) + bb.x,
-                                                    __uint_as_float(v[b][4 * qq + 1]) + bb.y);
-                            w[2 * qq + 1] = relu_bf16x2(__uint_as_float(v[b][4 * qq + 2]) + bb.z,
-                                                        __uint_as_float(v[b][4 * qq + 3]) + bb.w);
+                            w[2 * qq] = relu_bf16x2(__uint_as_float(v[4 * qq]) + bb.x, __uint_as_float(v[4 * qq + 1]) + bb.y);
+                            w[2 * qq + 1] =
+                                relu_bf16x2(__uint_as_float(v[4 * qq + 2]) + bb.z, __uint_as_float(v[4 * qq + 3]) + bb.w);
                         }
                         unsigned char *dst = dst0 + (size_t)(cb / 8) * 2048;
                         *reinterpret_cast<uint4 *>(dst) = make_uint4(w[0], w[1], w[2], w[3]);
                         *reinterpret_cast<uint4 *>(dst + 2048) = make_uint4(w[4], w[5], w[6], w[7]);
                     }
-                }
-                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-            } else {
-                float acc = 0.f;
-                for (int c0 = col_lo; c0 < col_hi; c0 += 32) {
-                    const int nb = min(2, (col_hi - c0) / 16);
-                    uint32_t v[2][16];
-                    tmem_ld_group<2>(taddr + (uint32_t)c0, nb, v);
-#pragma unroll
-                    for (int b = 0; b < 2; ++b) {
-                        if (b >= nb) break;
-                        const int cb = c0 + 16 * b;
+                    // the next layer's operand is written and this accumulator read: the issuer may go on
+                    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+                    mbar_arrive(&act_bar[t]);
+                } else {
+                    float acc = 0.f;
+                    for (int cb = col_lo; cb < col_hi; cb += 16) {
+                        uint32_t v[16];
+                        tmem_ld16(taddr + (uint32_t)cb, v);
 #pragma unroll
                         for (int qq = 0; qq < 4; ++qq) {
                             const float4 bb = reinterpret_cast<const float4 *>(bias + cb)[qq];
                             const float4 ww = reinterpret_cast<const float4 *>(par + 3 * H + cb)[qq];
-                            const uint32_t h01 = relu_bf16x2(__uint_as_float(v[b][4 * qq]) + bb.x,
-                                                             __uint_as_float(v[b][4 * qq + 1]) + bb.y);
-                            const uint32_t h23 = relu_bf16x2(__uint_as_float(v[b][4 * qq + 2]) + bb.z,
-                                                             __uint_as_float(v[b][4 * qq + 3]) + bb.w);
+                            const uint32_t h01 =
+                                relu_bf16x2(__uint_as_float(v[4 * qq]) + bb.x, __uint_as_float(v[4 * qq + 1]) + bb.y);
+                            const uint32_t h23 =
+                                relu_bf16x2(__uint_as_float(v[4 * qq + 2]) + bb.z, __uint_as_float(v[4 * qq + 3]) + bb.w);
                             acc = fmaf(__uint_as_float(h01 << 16), ww.x, acc);
                             acc = fmaf(__uint_as_float(h01 & 0xFFFF0000u), ww.y, acc);
                             acc = fmaf(__uint_as_float(h23 << 16), ww.z, acc);
                             acc = fmaf(__uint_as_float(h23 & 0xFFFF0000u), ww.w, acc);
                         }
                     }
+                    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+                    // the two column halves' dot products meet in this tile's (now free) activation buffer
+                    float *ypart = reinterpret_cast<float *>(act);
+                    ypart[half * 128 + row_in_tile] = acc;
+                    group_sync(bar_id);
+                    const int row = tile * 128 + row_in_tile;
+                    if (half == 0 && row < M) y[row] = (acc + ypart[128 + row_in_tile]) + par[4 * H];
+                    group_sync(bar_id);   // ypart read before the buffer takes the next input
                 }
-                // the two column halves' dot products meet in the (now free) activation buffer of tile 0
-                float *ypart = reinterpret_cast<float *>(smem + L.act0);
-                ypart[half * 256 + t_ep * 128 + row_in_tile] = acc;
-                __syncthreads();
-                const int row = (2 * pair + t_ep) * 128 + row_in_tile;
-                if (half == 0 && row < M) y[row] = (acc + ypart[256 + t_ep * 128 + row_in_tile]) + par[4 * H];
             }
-            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-            __syncthreads();
         }
     }
-    if (!ok) {
-        if (tid == 0) {
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if ((volatile int &)fail_sh) {
+        if (tid == FEPI) {
             atomicExch(err, 1u);
             // give copies and MMAs still in flight a bounded chance to land before TMEM is freed
-            for (long long j = consumed; j < loaded; ++j) {
+            for (long long j = consumed; j < (long long)loaded_sh; ++j) {
                 const int b = (int)(j % nbuf);
                 if (mbar_wait(&tma_bar[b], (tma_ph >> b) & 1u)) tma_ph ^= 1u << b;
             }
             tc_commit(&drain_bar);   // completes once every MMA this thread issued is done
             mbar_wait(&drain_bar, 0u);
         }
+        __syncthreads();
     }
-    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     if (warp == 0)
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(2 * TMEM_COLS) : "memory");
 }
