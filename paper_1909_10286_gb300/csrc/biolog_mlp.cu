@@ -267,17 +267,17 @@ gemm_bf16_tn_kernel(const __nv_bfloat16 *__restrict__ A, const __nv_bfloat16 *__
 //   rg, k block kb) at kb * 2048 + rg * 128 bytes   -> LBO 2048, SBO 128
 //   weight chunk: core matrix (n group ng, k block kb) at kb * (H * 16) + ng * 128
 //                                                      -> LBO H * 16, SBO 128
-// Roles (18 warps). The two tiles run a layer apart: while the tensor cores
-// work on one tile's layer, the other tile's epilogue runs.
+// Roles (18 warps). The two tiles run staggered: while the tensor cores work
+// on one tile's layer, the other tile's epilogue runs.
 //   warps 0-7 / 8-15: the epilogue group of tile A / B. Warp w of a group reads
 //     TMEM lanes 32 (w % 4) .. +31 of its tile's accumulator, column half
 //     (w / 4) % 2; the group stages its tile's input rows too.
-//   warp 16, lane 0: issues each layer's MMAs tile by tile (A, then B) as soon
-//     as the tile's operand is written and the chunk's weights have landed, and
-//     never waits for the tensor cores.
-//   warp 17, lane 0: refills the weight ring in the issuer's order (per pair:
-//     layer, tile, chunk -- each tile's layer streams its weights again): waits
-//     until a slot's MMAs are done and copies the next chunk into it.
+//   warp 16, lane 0: issues the tiles' layers in the order of fused_event, each
+//     as soon as the tile's operand is written, chunk by chunk as the weights
+//     land, and never waits for the tensor cores.
+//   warp 17, lane 0: refills the weight ring in the issuer's order (each tile's
+//     layer streams its weights again): waits until a slot's MMAs are done and
+//     copies the next chunk into it.
 // The issuer and the producer are alone in their warps: lanes of one warp that
 // wait on different barriers would take turns.
 constexpr int FGROUP = 256;                // threads of one epilogue group
@@ -456,6 +456,21 @@ __device__ __forceinline__ void mbar_arrive(uint64_t *bar)
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
 }
 
+// The issue order of the tiles' layers (0, 1, 2 = the three hidden layers), shared by the issuer
+// and the producer: event e of [0, 6 (P + 1)) is layer `layer` of tile `t`, or none. Per pair q:
+// A0(q) B2(q-1) A1(q) B0(q) A2(q) B1(q), and B2 of the last pair at the end. Tile B runs a layer
+// and a half behind tile A, so that each head epilogue (the longest) and most hidden-layer
+// epilogues overlap the other tile's long layers (K = H) rather than its short first layer.
+__device__ __forceinline__ bool fused_event(int e, int P, int &t, int &layer)
+{
+    const int q = e / 6, r = e % 6;
+    t = r & 1;
+    if (!t) { layer = r >> 1; return q < P; }
+    if (r == 1) { layer = 2; return q >= 1 && q <= P; }
+    layer = r == 3 ? 0 : 1;
+    return q < P;
+}
+
 // 18 warps: a sub-partition holds five of them, which caps a thread at 96 registers
 __global__ void __launch_bounds__(FTHREADS, 1)
 fused_mlp_forward_kernel(const __nv_bfloat16 *__restrict__ X, int M, int I, int H, const uint4 *__restrict__ wpack,
@@ -517,7 +532,7 @@ fused_mlp_forward_kernel(const __nv_bfloat16 *__restrict__ X, int M, int I, int 
 
     if (warp == FEPI / 32) {
         if (lane == 0) {
-            // ---- MMA issuer: per pair, layer by layer, tile A then tile B ----
+            // ---- MMA issuer: the tiles' layers in the order of fused_event ----
             const uint32_t idesc = instr_desc(128, H);
             // descriptors: the start-address field (bits 0-13, address >> 4) is added per operand
             const uint64_t a_tmpl = smem_desc(smem, 2048, 128) & ~0x3FFFull;
@@ -527,49 +542,49 @@ fused_mlp_forward_kernel(const __nv_bfloat16 *__restrict__ X, int M, int I, int 
             uint32_t act_ph = 0;   // bit t: parity of the next wait on act_bar[t]
             int cb = 0;            // ring slot of the next chunk
             bool good = true;
-            for (int p = 0; p < my_pairs && good; ++p)
-                for (int layer = 0; layer < 3 && good; ++layer) {
-                    const int nch = layer == 0 ? nch1 : nch2, jj0 = layer == 0 ? 0 : (layer == 1 ? nch1 : nch1 + nch2);
-                    for (int t = 0; t < 2 && good; ++t) {
-                        // tile t's operand (its input, or the previous layer's epilogue) is in place, and that
-                        // epilogue has read its accumulator
-                        if (failed() || !mbar_wait(&act_bar[t], (act_ph >> t) & 1u)) { good = false; break; }
-                        act_ph ^= 1u << t;
-                        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-                        const uint32_t a_addr = t ? a_addr1 : a_addr0, acc_t = tmem + (uint32_t)(t * TMEM_COLS);
-                        for (int c = 0; c < nch; ++c) {
-                            if (!mbar_wait(&tma_bar[cb], (tma_ph >> cb) & 1u)) { good = false; break; }
-                            tma_ph ^= 1u << cb;
-                            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-                            int lay, cc, kc;
-                            size_t off;
-                            fused_chunk(G, H, jj0 + c, lay, cc, kc, off);
-                            const int K = lay == 0 ? I : H;
-                            const uint32_t bsl = w_addr + (uint32_t)(cb * (buf_bytes >> 4));
-                            const int ns = (min(kc, K - cc * kc) + 15) / 16;   // K steps of 16 (zero padded past K)
-                            for (int s = 0; s < ns; ++s) {
-                                const int k = cc * kc + s * 16;
-                                const uint64_t bd = b_tmpl | (uint64_t)(bsl + (uint32_t)(2 * s * H));   // (2 s H 16) >> 4
-                                const uint32_t ko = (uint32_t)(k / 8) * (2048 >> 4);
-                                tc_mma(acc_t, a_tmpl | (uint64_t)(a_addr + ko), bd, idesc, (cc > 0 || s > 0) ? 1u : 0u);
-                            }
-                            tc_commit(&mma_bar[cb]);
-                            ++consumed;
-                            cb = cb + 1 == nbuf ? 0 : cb + 1;
-                        }
-                        if (good) tc_commit(&acc_bar[t]);
+            for (int e = 0; e < 6 * (my_pairs + 1) && good; ++e) {
+                int t, layer;
+                if (!fused_event(e, my_pairs, t, layer)) continue;
+                const int nch = layer == 0 ? nch1 : nch2, jj0 = layer == 0 ? 0 : (layer == 1 ? nch1 : nch1 + nch2);
+                // tile t's operand (its input, or the previous layer's epilogue) is in place, and that
+                // epilogue has read its accumulator
+                if (failed() || !mbar_wait(&act_bar[t], (act_ph >> t) & 1u)) { good = false; break; }
+                act_ph ^= 1u << t;
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                const uint32_t a_addr = t ? a_addr1 : a_addr0, acc_t = tmem + (uint32_t)(t * TMEM_COLS);
+                for (int c = 0; c < nch; ++c) {
+                    if (!mbar_wait(&tma_bar[cb], (tma_ph >> cb) & 1u)) { good = false; break; }
+                    tma_ph ^= 1u << cb;
+                    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                    int lay, cc, kc;
+                    size_t off;
+                    fused_chunk(G, H, jj0 + c, lay, cc, kc, off);
+                    const int K = lay == 0 ? I : H;
+                    const uint32_t bsl = w_addr + (uint32_t)(cb * (buf_bytes >> 4));
+                    const int ns = (min(kc, K - cc * kc) + 15) / 16;   // K steps of 16 (zero padded past K)
+                    for (int s = 0; s < ns; ++s) {
+                        const int k = cc * kc + s * 16;
+                        const uint64_t bd = b_tmpl | (uint64_t)(bsl + (uint32_t)(2 * s * H));   // (2 s H 16) >> 4
+                        const uint32_t ko = (uint32_t)(k / 8) * (2048 >> 4);
+                        tc_mma(acc_t, a_tmpl | (uint64_t)(a_addr + ko), bd, idesc, (cc > 0 || s > 0) ? 1u : 0u);
                     }
+                    tc_commit(&mma_bar[cb]);
+                    ++consumed;
+                    cb = cb + 1 == nbuf ? 0 : cb + 1;
                 }
+                if (good) tc_commit(&acc_bar[t]);
+            }
             if (!good) fail_sh = 1;
         }
         __syncwarp();
     } else if (warp == FEPI / 32 + 1) {
         if (lane == 0) {
-            // ---- weight producer: the chunks in the issuer's order (per pair: layer, tile, chunk) ----
+            // ---- weight producer: the chunks in the issuer's order (fused_event, then chunk) ----
             const long long total = (long long)my_pairs * 2 * cpt;
             long long loaded = 0;
             uint32_t mma_ph = 0;   // bit b: parity of the next wait on mma_bar[b]
-            int lb = 0, layer = 0, t = 0, c = 0;
+            int lb = 0, e = 0, t = 0, layer = 0, c = 0;
+            while (e < 6 * (my_pairs + 1) && !fused_event(e, my_pairs, t, layer)) ++e;
             for (; loaded < total; ++loaded) {
                 // slot lb's previous chunk (loaded - nbuf) must be consumed first
                 if (loaded >= nbuf) {
@@ -585,7 +600,8 @@ fused_mlp_forward_kernel(const __nv_bfloat16 *__restrict__ X, int M, int I, int 
                 lb = lb + 1 == nbuf ? 0 : lb + 1;
                 if (++c == (layer == 0 ? nch1 : nch2)) {
                     c = 0;
-                    if (++t == 2) { t = 0; layer = layer == 2 ? 0 : layer + 1; }
+                    do ++e;
+                    while (e < 6 * (my_pairs + 1) && !fused_event(e, my_pairs, t, layer));
                 }
             }
             loaded_sh = (unsigned long long)loaded;
