@@ -139,22 +139,23 @@ def study(workload: str = "paper", seeds=range(10), n: int = 1 << 20, iters: int
 
 def _wall_to_target(S, targets, max_iters, step):
     """Host wall time, through the API, until each instance's C* is within its target: one iteration per
-    call, C* read back from the log after each. Returns (ms per instance or None, iterations per
-    instance or None, total iterations run, total ms)."""
+    call, then every instance's C* read back in one transfer (bl_get_states). Returns (ms per instance or
+    None, iterations per instance or None, total iterations run, total ms)."""
     n_inst = len(targets)
     reached_ms = [None] * n_inst
     reached_it = [None] * n_inst
-    c0 = [S.get_state(inst=k)["cstar"] for k in range(n_inst)]
+    states = S.get_states()
     for k in range(n_inst):
-        if c0[k] <= targets[k]:
+        if states[k]["cstar"] <= targets[k]:
             reached_ms[k], reached_it[k] = 0.0, 0
     t0 = time.perf_counter()
     it = 0
     while it < max_iters and any(r is None for r in reached_ms):
         step(1)
         it += 1
+        S.get_states(states)
         for k in range(n_inst):
-            if reached_ms[k] is None and float(S.get_log(it - 1, 1, inst=k)["cstar"][0]) <= targets[k]:
+            if reached_ms[k] is None and float(states[k]["cstar"]) <= targets[k]:
                 reached_ms[k] = (time.perf_counter() - t0) * 1e3
                 reached_it[k] = it
     return reached_ms, reached_it, it, (time.perf_counter() - t0) * 1e3
@@ -164,13 +165,14 @@ def study_wall(workload: str = "large", seeds=range(5), n: int = 1 << 20, n_batc
                max_iters: int = 400, ref_iters: int = 4000, ref_n: int = 1 << 16, pool: int = 1 << 18,
                keep: int = 2359, rand_frac: float = 0.001, train_seeds=range(100, 104), train_iters: int = 30,
                train_sample: int = 8192, train_steps: int = 1500, tol: float = 0.01, eps: float = 0.5,
-               seed_offset: int = 1000, k_values=(1, 2)) -> dict:
+               seed_offset: int = 1000, k_values=(1, 2), forms=None) -> dict:
     """Time to within `tol` of the best cost, measured as host wall time through the API (every
-    iteration a bl_search_step call and a read of C*), from handles already set up; set-up and the
+    iteration a bl_search_step call and one read of every instance's C*), from handles already set up; set-up and the
     ranker's training are reported beside it, not counted. C_ref per instance is the best C* of a
     plain batched run of ref_iters iterations of ref_n candidates. Forms: plain (one handle per
     instance, run one after the other) and batched (all instances in one launch per iteration) with
-    k = 1, 2 ... chained moves per candidate, and learned + batched (MLP-ranked proposals)."""
+    k = 1, 2 ... chained moves per candidate, and learned + batched (MLP-ranked proposals). `forms`, if
+    given, names the forms to run (e.g. ("batched", "plain_k2", "learned_batched"))."""
     import torch
 
     insts = I.make_batch(workload, seeds)
@@ -179,6 +181,11 @@ def study_wall(workload: str = "large", seeds=range(5), n: int = 1 << 20, n_batc
     c_ref = _final_best(insts, biolog.make_params(n_cand=ref_n, seed=seed_offset, **kw), ref_iters)
     t_ref = time.time() - t0
     targets = [(1 + tol) * c for c in c_ref]
+    wanted = None if forms is None else frozenset(forms)
+
+    def want(name):
+        return wanted is None or name in wanted
+
     forms = {}
 
     def summarise(name, ms, its, total_ms, setup_s, sequential, **extra):
@@ -191,13 +198,15 @@ def study_wall(workload: str = "large", seeds=range(5), n: int = 1 << 20, n_batc
 
     # warm the kernels of every form once (module loading, attributes), outside the timed runs
     for k in k_values:
+        if not (want("plain" if k == 1 else f"plain_k{k}") or want("batched" if k == 1 else f"batched_k{k}")):
+            continue
         W = biolog.Search(insts[:1], biolog.make_params(n_cand=4096, seed=seed_offset, k_moves=k, **kw))
         W.search_step(2)
         W.close()
     for k in k_values:
         suffix = "" if k == 1 else f"_k{k}"
         ms_all, it_all, run_ms, setup = [], [], 0.0, 0.0
-        for s, inst, tg in zip(seeds, insts, targets):
+        for s, inst, tg in zip(seeds, insts, targets) if want("plain" + suffix) else ():
             t1 = time.time()
             S = biolog.Search([inst], biolog.make_params(n_cand=n, seed=seed_offset + int(s), k_moves=k, **kw))
             torch.cuda.synchronize()
@@ -207,7 +216,10 @@ def study_wall(workload: str = "large", seeds=range(5), n: int = 1 << 20, n_batc
             it_all += its
             run_ms += tot
             S.close()
-        summarise("plain" + suffix, ms_all, it_all, run_ms, setup, True, n_cand=n, k_moves=k)
+        if want("plain" + suffix):
+            summarise("plain" + suffix, ms_all, it_all, run_ms, setup, True, n_cand=n, k_moves=k)
+        if not want("batched" + suffix):
+            continue
         t1 = time.time()
         S = biolog.Search(insts, biolog.make_params(n_cand=n_batched, seed=seed_offset, k_moves=k, **kw))
         torch.cuda.synchronize()
@@ -216,25 +228,26 @@ def study_wall(workload: str = "large", seeds=range(5), n: int = 1 << 20, n_batc
         S.close()
         summarise("batched" + suffix, ms, its, tot, setup, False, n_cand=n_batched, k_moves=k)
 
-    t1 = time.time()
-    X, T = learned.collect(I.make_batch(workload, train_seeds), iters=train_iters, sample=train_sample)
-    net, losses = learned.train(X, T, hidden=256, steps=train_steps, batch=4096, lr=1e-3,
-                                max_batch=pool * len(insts))
-    t_train = time.time() - t1
-    t1 = time.time()
-    S = biolog.Search(insts, biolog.make_params(n_cand=pool, seed=seed_offset, **kw))
-    netS = net.copy(stream=S.stream, max_batch=pool * len(insts))
-    torch.cuda.synchronize()
-    setup = time.time() - t1
-    ms, its, _, tot = _wall_to_target(S, targets, max_iters,
-                                      lambda c: S.search_step_learned(netS, c, pool, keep, rand_frac))
-    netS.close()
-    S.close()
-    net.close()
-    summarise("learned_batched", ms, its, tot, setup, False, pool=pool, keep=keep, rand_frac=rand_frac,
-              train_tuples=int(X.shape[0]), train_s=round(t_train, 1),
-              train_loss_first_last=[float(np.mean(losses[:50])), float(np.mean(losses[-50:]))])
+    if want("learned_batched"):
+        t1 = time.time()
+        X, T = learned.collect(I.make_batch(workload, train_seeds), iters=train_iters, sample=train_sample)
+        net, losses = learned.train(X, T, hidden=256, steps=train_steps, batch=4096, lr=1e-3,
+                                    max_batch=pool * len(insts))
+        t_train = time.time() - t1
+        t1 = time.time()
+        S = biolog.Search(insts, biolog.make_params(n_cand=pool, seed=seed_offset, **kw))
+        netS = net.copy(stream=S.stream, max_batch=pool * len(insts))
+        torch.cuda.synchronize()
+        setup = time.time() - t1
+        ms, its, _, tot = _wall_to_target(S, targets, max_iters,
+                                          lambda c: S.search_step_learned(netS, c, pool, keep, rand_frac))
+        netS.close()
+        S.close()
+        net.close()
+        summarise("learned_batched", ms, its, tot, setup, False, pool=pool, keep=keep, rand_frac=rand_frac,
+                  train_tuples=int(X.shape[0]), train_s=round(t_train, 1),
+                  train_loss_first_last=[float(np.mean(losses[:50])), float(np.mean(losses[-50:]))])
     return dict(workload=workload, seeds=[int(s) for s in seeds], tol=tol, max_iters=max_iters,
                 c_ref=[float(c) for c in c_ref], c_ref_run=dict(n_cand=ref_n, iters=ref_iters, s=round(t_ref, 1)),
-                timing="host wall clock through the API: one bl_search_step call and one C* read per iteration",
+                timing="host wall clock through the API: per iteration one bl_search_step call and one bl_get_states read of every instance's C*",
                 forms=forms)
