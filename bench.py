@@ -41,6 +41,18 @@ WORKLOAD_BATCHED = ("batched uneven instances: 256 instances (fields U{10..120},
 WORKLOAD_LARGE = ("large plain search: 300 fields, 20 BPs, 10 tours, 60 HUs, 120 SUs, 150x150 km, "
                   "2^24 candidates/iter")
 L2_FLUSH_BYTES = 256 << 20
+
+
+def workload_text(workload: str, n_inst: int, n_per_inst: int) -> str:
+    """The workload description with the instance count and candidates per iteration actually run."""
+    k = n_per_inst.bit_length() - 1
+    n = f"2^{k}" if n_per_inst == 1 << k else str(n_per_inst)
+    base = {"paper": WORKLOAD, "batched": WORKLOAD_BATCHED, "large": WORKLOAD_LARGE}.get(workload)
+    if base is None:
+        return workload
+    if workload == "batched":
+        return base.replace("256 instances", f"{n_inst} instances").replace("2^16 candidates", f"{n} candidates")
+    return base.replace("2^20 candidates", f"{n} candidates").replace("2^24 candidates", f"{n} candidates")
 # time-to-1% study settings per workload (paper: seeds 0-9, the paper's 10 experiments)
 STUDY = {
     "paper": dict(workload="paper", seeds=range(10), n=1 << 20, iters=300, budget=1000, n_batched=1 << 16,
@@ -533,7 +545,9 @@ def main():
 
             r = time_to_target.study_wall(**STUDY_WALL)
             line["time_to_1pct"] = {
-                "unit": "ms", "higher_is_better": False, "workload": WORKLOAD_LARGE, "tol": r["tol"],
+                "unit": "ms", "higher_is_better": False,
+                "workload": "large instances (300 fields, 20 BPs, 10 tours, 60 HUs, 120 SUs, 150x150 km); "
+                            "candidates per iteration of each form in `forms`", "tol": r["tol"],
                 "instances": r["seeds"], "timing": r["timing"],
                 "c_ref": f"best C* of a plain batched run of {r['c_ref_run']['iters']} iterations of "
                          f"{r['c_ref_run']['n_cand']} candidates per instance",
@@ -632,8 +646,7 @@ def measure_plain(args, workload, ws, rank, local, cpu_budget):
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": {"paper": WORKLOAD, "batched": WORKLOAD_BATCHED,
-                                    "large": WORKLOAD_LARGE}.get(workload, workload),
+            "config": {"workload": workload_text(workload, len(insts), n_total // max(1, len(insts))),
                        "instance_seed": args.seed, "n_instances": len(insts), "n_cand_per_iter": n_total,
                        "eps": 0.5, "gate": 1, "autotuned": tuned,
                        "l2": "flushed before every timed step (256 MiB device write)",
