@@ -43,15 +43,19 @@ WORKLOAD_LARGE = ("large plain search: 300 fields, 20 BPs, 10 tours, 60 HUs, 120
 L2_FLUSH_BYTES = 256 << 20
 
 
-def workload_text(workload: str, n_inst: int, n_per_inst: int) -> str:
-    """The workload description with the instance count and candidates per iteration actually run."""
+def workload_text(workload: str, n_inst: int, n_per_inst: int, n_groups: int = 1) -> str:
+    """The workload description with the instance count, candidates per iteration and launches actually run."""
     k = n_per_inst.bit_length() - 1
     n = f"2^{k}" if n_per_inst == 1 << k else str(n_per_inst)
     base = {"paper": WORKLOAD, "batched": WORKLOAD_BATCHED, "large": WORKLOAD_LARGE}.get(workload)
     if base is None:
         return workload
     if workload == "batched":
-        return base.replace("256 instances", f"{n_inst} instances").replace("2^16 candidates", f"{n} candidates")
+        base = base.replace("256 instances", f"{n_inst} instances").replace("2^16 candidates", f"{n} candidates")
+        if n_groups > 1:
+            base = base.replace("one launch per iteration",
+                                f"one launch per iteration for each of {n_groups} launch-shape groups")
+        return base
     return base.replace("2^20 candidates", f"{n} candidates").replace("2^24 candidates", f"{n} candidates")
 # time-to-1% study settings per workload (paper: seeds 0-9, the paper's 10 experiments)
 STUDY = {
@@ -500,6 +504,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--n-inst", type=int, default=256, help="instances of the batched workload")
     ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--no-shape-split", action="store_true",
+                    help="batched: one handle for the whole batch instead of one per launch shape")
     ap.add_argument("--no-time-to-target", action="store_true",
                     help="skip the time-to-1%% study (paper workload, rank 0, one GPU)")
     ap.add_argument("--no-extra-lines", action="store_true",
@@ -588,19 +594,26 @@ def measure_plain(args, workload, ws, rank, local, cpu_budget):
     stream = torch.cuda.Stream()
     tuned = None
     insts = rank_instances(workload, args.seed, rank, args.n_inst)
-    if workload == "batched":
-        if args.no_autotune:
-            params = biolog.make_params(n_cand=n, **kw)
-        else:
-            from paper_1909_10286_gb300 import autotune
-            tuned = autotune.tune(insts, n, base_params=kw)
-            params = biolog.make_params(n_cand=n, blocks_per_sm=tuned["blocks_per_sm"], tile=tuned["tile"],
-                                        lanes_per_cand=tuned.get("lanes_per_cand", 1), **kw)
-    else:
-        params = biolog.make_params(n_cand=n, **kw)
+    tuned_all = []
+
+    def params_of(group):
+        if workload != "batched" or args.no_autotune:
+            return biolog.make_params(n_cand=n, **kw)
+        from paper_1909_10286_gb300 import autotune
+        t = autotune.tune(group, n, base_params=kw)
+        tuned_all.append(t)
+        return biolog.make_params(n_cand=n, blocks_per_sm=t["blocks_per_sm"], tile=t["tile"],
+                                  lanes_per_cand=t.get("lanes_per_cand", 1), **kw)
+
     inst = insts[0]
     n_total = n * len(insts)
-    S = biolog.Search(insts, params, stream=stream)
+    if workload == "batched" and not args.no_shape_split:
+        # one handle per launch shape (the instances that fit the four-tour shape, and the rest)
+        from paper_1909_10286_gb300 import shaped
+        S = shaped.ShapedBatch(insts, params_of, stream=stream)
+    else:
+        S = biolog.Search(insts, params_of(insts), stream=stream)
+    tuned = (tuned_all[0] if len(tuned_all) == 1 else tuned_all) or None
     cfg = S.config()
     with torch.cuda.stream(stream):
         S.search_step(args.warmup)
@@ -646,7 +659,8 @@ def measure_plain(args, workload, ws, rank, local, cpu_budget):
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": workload_text(workload, len(insts), n_total // max(1, len(insts))),
+            "config": {"workload": workload_text(workload, len(insts), n_total // max(1, len(insts)),
+                                                 len(cfg.get("groups", [cfg]))),
                        "instance_seed": args.seed, "n_instances": len(insts), "n_cand_per_iter": n_total,
                        "eps": 0.5, "gate": 1, "autotuned": tuned,
                        "l2": "flushed before every timed step (256 MiB device write)",
@@ -671,7 +685,9 @@ def measure_plain(args, workload, ws, rank, local, cpu_budget):
         peak = sms * 4 * 32 * f_mhz * 1e6 / 1e12            # lane-ops/s: 4 schedulers x 32 lanes per SM
         achieved = w_per * n_total / (ms_step / 1e3) / 1e12
         line["roofline"] = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tlane-op/s",
-                            "frac": achieved / peak, "traffic": _traffic(workload), "ops_per_candidate": w_per,
+                            "frac": achieved / peak,
+                            "traffic": _traffic("batched_one" if workload == "batched" and args.no_shape_split
+                                                else workload), "ops_per_candidate": w_per,
                             "peak_basis": f"{sms} SMs x 4 schedulers x 32 lanes x {f_mhz:.0f} MHz (sm_max_mhz of "
                                           "MEASURED_PEAKS.json)"}
         if len(insts) > 1:
