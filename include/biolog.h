@@ -160,7 +160,12 @@ int bl_plan_init(const bl_instance *inst, const bl_params *params, void *cuda_st
 /* Same for n_inst independent instances of uneven size searched together:
    one persistent launch per iteration covers all of them (work items ordered
    largest instance first), each with its own x_old, x*, C*, Tmax* and
-   Philox counter word inst_idx+k. */
+   Philox counter word inst_idx+k. The launch shape (threads per block, tour
+   and unit capacity, distances in shared memory or read through L2) is the
+   one the largest instance needs, for every instance of the handle. Small
+   instances of an uneven batch run faster on a handle of their own: e.g.
+   those with at most 4 tours and 32 HUs and SUs take the 256-thread shape.
+   Handles on one stream run one after another. */
 int bl_plan_init_batch(const bl_instance *insts, int32_t n_inst, const bl_params *params, void *cuda_stream,
                        bl_handle **out);
 
