@@ -545,29 +545,34 @@ fused_mlp_forward_kernel(const __nv_bfloat16 *__restrict__ X, int M, int I, int 
             for (int e = 0; e < 6 * (my_pairs + 1) && good; ++e) {
                 int t, layer;
                 if (!fused_event(e, my_pairs, t, layer)) continue;
-                const int nch = layer == 0 ? nch1 : nch2, jj0 = layer == 0 ? 0 : (layer == 1 ? nch1 : nch1 + nch2);
+                const int nch = layer == 0 ? nch1 : nch2;
                 // tile t's operand (its input, or the previous layer's epilogue) is in place, and that
                 // epilogue has read its accumulator
                 if (failed() || !mbar_wait(&act_bar[t], (act_ph >> t) & 1u)) { good = false; break; }
                 act_ph ^= 1u << t;
                 asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
                 const uint32_t a_addr = t ? a_addr1 : a_addr0, acc_t = tmem + (uint32_t)(t * TMEM_COLS);
-                for (int c = 0; c < nch; ++c) {
+                // K steps of 16 in the layer and per full chunk (zero padded past K). A's descriptor advances
+                // 256 per step (two 2048-byte core-matrix blocks), the chunk's 2 H (two H * 16-byte blocks).
+                // The chunk geometry is fixed per layer, so only the wait, the fence and the commit sit
+                // between one chunk's MMAs and the next's (an address field stays below 2^14, so + is |).
+                const int K = layer == 0 ? I : H, spc = (layer == 0 ? G.k1 : G.k2) / 16, nsteps = (K + 15) / 16;
+                uint64_t ad = a_tmpl + (uint64_t)a_addr;
+                for (int c = 0, s0 = 0; c < nch; ++c, s0 += spc) {
                     if (!mbar_wait(&tma_bar[cb], (tma_ph >> cb) & 1u)) { good = false; break; }
                     tma_ph ^= 1u << cb;
                     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-                    int lay, cc, kc;
-                    size_t off;
-                    fused_chunk(G, H, jj0 + c, lay, cc, kc, off);
-                    const int K = lay == 0 ? I : H;
-                    const uint32_t bsl = w_addr + (uint32_t)(cb * (buf_bytes >> 4));
-                    const int ns = (min(kc, K - cc * kc) + 15) / 16;   // K steps of 16 (zero padded past K)
-                    for (int s = 0; s < ns; ++s) {
-                        const int k = cc * kc + s * 16;
-                        const uint64_t bd = b_tmpl | (uint64_t)(bsl + (uint32_t)(2 * s * H));   // (2 s H 16) >> 4
-                        const uint32_t ko = (uint32_t)(k / 8) * (2048 >> 4);
-                        tc_mma(acc_t, a_tmpl | (uint64_t)(a_addr + ko), bd, idesc, (cc > 0 || s > 0) ? 1u : 0u);
+                    const uint64_t bd = b_tmpl + (uint64_t)(w_addr + (uint32_t)cb * (buf_bytes >> 4));
+                    const int ns = min(spc, nsteps - s0);
+                    if (ns == 4) {
+#pragma unroll
+                        for (int s = 0; s < 4; ++s)
+                            tc_mma(acc_t, ad + 256u * s, bd + (uint64_t)(2 * s * H), idesc, (s0 + s) > 0 ? 1u : 0u);
+                    } else {
+                        for (int s = 0; s < ns; ++s)
+                            tc_mma(acc_t, ad + 256u * s, bd + (uint64_t)(2 * s * H), idesc, (s0 + s) > 0 ? 1u : 0u);
                     }
+                    ad += 256u * ns;
                     tc_commit(&mma_bar[cb]);
                     ++consumed;
                     cb = cb + 1 == nbuf ? 0 : cb + 1;
