@@ -186,6 +186,7 @@ class Search:
                                       C.byref(h))
         _check(rc)
         self.h = h
+        self._states_c = None   # (array ids, ctypes bl_state array, the arrays) of the last packed transfer
 
     # --- the three calls of the paper's loop
     def search_step(self, n_iters: int):
@@ -242,11 +243,23 @@ class Search:
             out.append(dict(xold=tuple(a[:4]), xbest=tuple(a[4:]), cstar=0.0, tmaxstar=0.0, iter=0))
         return out
 
+    def _states_struct(self, arrays):
+        """The ctypes bl_state array pointing at `arrays` (per instance: x_old's four, then x*'s four).
+        Built once and reused while the same arrays come back, as in a loop that passes one state list
+        to every bl_set_states / bl_get_states; the library reads and writes them through the pointers."""
+        key = [tuple(id(x) for x in a) for a in arrays]
+        c = self._states_c
+        if c is not None and c[0] == key:
+            return c[1]
+        arr = (bl_state * len(arrays))(*[bl_state(*[_p(x) for x in a], 0.0, 0.0, 0) for a in arrays])
+        self._states_c = (key, arr, arrays)   # the arrays stay referenced while the pointers are kept
+        return arr
+
     def get_states(self, out=None) -> list:
         """bl_get_states: every instance's state in one transfer; fills and returns `out` (a list of state
         dicts as get_state returns, e.g. from an earlier call) or new arrays."""
         out = out if out is not None else self._state_arrays()
-        arr = (bl_state * len(out))(*[bl_state(*[_p(x) for x in (*o["xold"], *o["xbest"])], 0.0, 0.0, 0) for o in out])
+        arr = self._states_struct([(*o["xold"], *o["xbest"]) for o in out])
         _check(load().bl_get_states(self.h, C.cast(arr, C.c_void_p)), self.h)
         for o, s in zip(out, arr):
             o.update(cstar=s.cstar, tmaxstar=s.tmaxstar, iter=s.iter)
@@ -254,9 +267,13 @@ class Search:
 
     def set_states(self, states: list):
         """bl_set_states: every instance's state in one transfer."""
-        keep = [[np.ascontiguousarray(x, dtype=np.int16) for x in (*st["xold"], *st["xbest"])] for st in states]
-        arr = (bl_state * len(states))(*[bl_state(*[_p(x) for x in a], float(st["cstar"]), float(st["tmaxstar"]),
-                                                  int(st["iter"])) for a, st in zip(keep, states)])
+        def i16(x):
+            ok = isinstance(x, np.ndarray) and x.dtype == np.int16 and x.flags.c_contiguous
+            return x if ok else np.ascontiguousarray(x, dtype=np.int16)
+
+        arr = self._states_struct([tuple(i16(x) for x in (*st["xold"], *st["xbest"])) for st in states])
+        for s, st in zip(arr, states):
+            s.cstar, s.tmaxstar, s.iter = float(st["cstar"]), float(st["tmaxstar"]), int(st["iter"])
         _check(load().bl_set_states(self.h, C.cast(arr, C.c_void_p)), self.h)
 
     def get_log(self, first: int, n: int, inst: int = 0) -> dict:

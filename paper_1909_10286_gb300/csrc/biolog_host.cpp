@@ -355,8 +355,12 @@ struct bl_handle {
     float *l_y = nullptr, *l_thresh = nullptr;
     uint32_t *l_list = nullptr;
     int32_t *l_count = nullptr;
-    unsigned char *h_states = nullptr;   // pinned staging of bl_get_states / bl_set_states (first use)
+    // pinned staging of bl_set_states (h_states) and bl_get_states (h_states_out), allocated at first use;
+    // states_in_done: recorded after bl_set_states' copy out of h_states, so that the next one waits only
+    // for that copy and bl_get_states for nothing but its own transfer
+    unsigned char *h_states = nullptr, *h_states_out = nullptr;
     size_t states_bytes = 0;
+    cudaEvent_t states_in_done = nullptr;
     int dev = -1;                      // the device current at plan_init
     void *noalloc_scratch = nullptr;   // device address of bl_argmin_noalloc's static scratch (first call)
     std::string err;
@@ -880,11 +884,17 @@ size_t states_layout(const bl_handle *h, std::vector<int32_t> &offs)
 int states_staging(bl_handle *h, size_t bytes)
 {
     if (bytes > kScratchBytes) { h->err = "too many instances for one packed state transfer"; return BL_ETOO_LARGE; }
+    if (!h->states_in_done) CK(h, cudaEventCreateWithFlags(&h->states_in_done, cudaEventDisableTiming));
     if (h->states_bytes < bytes) {
-        if (h->h_states) cudaFreeHost(h->h_states);
-        h->h_states = nullptr;
+        if (h->h_states) {
+            CK(h, cudaStreamSynchronize(h->stream));   // a copy out of the old staging may still be queued
+            cudaFreeHost(h->h_states);
+        }
+        h->h_states = h->h_states_out = nullptr;
         h->states_bytes = 0;
-        CK(h, cudaMallocHost((void **)&h->h_states, bytes));
+        const size_t half = align_up(bytes, 256);
+        CK(h, cudaMallocHost((void **)&h->h_states, 2 * half));
+        h->h_states_out = h->h_states + half;
         h->states_bytes = bytes;
     }
     return BL_OK;
@@ -899,18 +909,19 @@ int bl_get_states(bl_handle *h, bl_state *out)
     const size_t bytes = states_layout(h, offs);
     int rc = states_staging(h, bytes);
     if (rc != BL_OK) return rc;
-    // the staging buffer may still feed an earlier bl_set_states copy on the stream
-    CK(h, cudaStreamSynchronize(h->stream));
+    // its own staging: no earlier copy reads it (every bl_get_states ends synchronised), so the offsets,
+    // the pack and the copy back queue behind the stream's work with one synchronisation at the end
     unsigned char *d = h->at<unsigned char>(h->ws.scratch);
-    std::memcpy(h->h_states, offs.data(), 4 * offs.size());
-    CK(h, cudaMemcpyAsync(d, h->h_states, 4 * offs.size(), cudaMemcpyHostToDevice, h->stream));
+    unsigned char *hs = h->h_states_out;
+    std::memcpy(hs, offs.data(), 4 * offs.size());
+    CK(h, cudaMemcpyAsync(d, hs, 4 * offs.size(), cudaMemcpyHostToDevice, h->stream));
     CK(h, launch_state_pack(h->at<InstMeta>(h->ws.meta), h->n_inst, (const int32_t *)d, d, 0, h->stream));
-    CK(h, cudaMemcpyAsync(h->h_states, d, bytes, cudaMemcpyDeviceToHost, h->stream));
+    CK(h, cudaMemcpyAsync(hs, d, bytes, cudaMemcpyDeviceToHost, h->stream));
     CK(h, cudaStreamSynchronize(h->stream));
     for (int k = 0; k < h->n_inst; ++k) {
         const HostInst &hi = h->insts[(size_t)k];
         const int B = hi.B, T = hi.T, F = hi.F;
-        const int16_t *p = (const int16_t *)(h->h_states + offs[(size_t)k]);
+        const int16_t *p = (const int16_t *)(hs + offs[(size_t)k]);
         InstState st;
         std::memcpy(&st, p + 2 * hi.plan_len, sizeof(st));
         if (st.error) return state_error(h, st.error, k);
@@ -951,8 +962,8 @@ int bl_set_states(bl_handle *h, const bl_state *in)
     const size_t bytes = states_layout(h, offs);
     int rc = states_staging(h, bytes);
     if (rc != BL_OK) return rc;
-    // the staging buffer may still feed an earlier copy on the stream
-    CK(h, cudaStreamSynchronize(h->stream));
+    // the staging may still feed the previous bl_set_states' copy: wait for that copy only
+    CK(h, cudaEventSynchronize(h->states_in_done));
     std::memcpy(h->h_states, offs.data(), 4 * offs.size());
     for (int k = 0; k < h->n_inst; ++k) {
         const HostInst &hi = h->insts[(size_t)k];
@@ -974,6 +985,7 @@ int bl_set_states(bl_handle *h, const bl_state *in)
     }
     unsigned char *d = h->at<unsigned char>(h->ws.scratch);
     CK(h, cudaMemcpyAsync(d, h->h_states, bytes, cudaMemcpyHostToDevice, h->stream));
+    CK(h, cudaEventRecord(h->states_in_done, h->stream));
     CK(h, launch_state_pack(h->at<InstMeta>(h->ws.meta), h->n_inst, (const int32_t *)d, d, 1, h->stream));
     return BL_OK;
 }
@@ -1304,6 +1316,7 @@ int bl_plan_free(bl_handle *h)
     if (h->stream || h->base) cudaStreamSynchronize(h->stream);
     if (h->graph) cudaGraphExecDestroy(h->graph);
     if (h->h_states) cudaFreeHost(h->h_states);
+    if (h->states_in_done) cudaEventDestroy(h->states_in_done);
     if (h->capture_stream) cudaStreamDestroy(h->capture_stream);
     if (h->own_ws && h->base) cudaFree(h->base);
     if (h->l_feat) cudaFree(h->l_feat);

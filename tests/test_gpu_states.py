@@ -48,3 +48,32 @@ def test_packed_states_equal_the_per_instance_calls_and_resume_exactly():
         assert _same(after[k], res[k])
     A.close()
     B.close()
+
+
+def test_packed_state_calls_read_and_write_the_arrays_passed_each_time():
+    """The binding keeps the ctypes state array while the same arrays come back: an edit made in place
+    between calls is what bl_set_states takes, bl_get_states refills the same arrays, and other arrays
+    (copies) are used as given."""
+    insts = I.make_batch("batched", range(8, 11))
+    A = biolog.Search(insts, biolog.make_params(n_cand=4096, **KW))
+    A.search_step(4)
+    st = A.get_states()
+    arrays = [a for s in st for a in (*s["xold"], *s["xbest"])]
+    for a, b in zip(st[1]["xold"], st[1]["xbest"]):
+        a[:] = b                                    # x_old := x* of instance 1, in place
+    st[1]["iter"] = 77
+    A.set_states(st)
+    one = A.get_state(inst=1)
+    assert gpu_plan(one, "xold") == gpu_plan(one, "xbest") and one["iter"] == 77
+    A.search_step(2)
+    st2 = A.get_states(st)
+    assert st2 is st and all(x is y for x, y in zip([a for s in st2 for a in (*s["xold"], *s["xbest"])], arrays))
+    for k in range(len(insts)):
+        assert _same(st2[k], A.get_state(inst=k))
+    copies = [dict(s, xold=tuple(a.copy() for a in s["xold"]), xbest=tuple(a.copy() for a in s["xbest"]))
+              for s in st2]
+    A.search_step(3)
+    A.set_states(copies)
+    for k in range(len(insts)):
+        assert _same(A.get_state(inst=k), copies[k])
+    A.close()
