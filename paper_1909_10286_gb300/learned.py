@@ -29,8 +29,11 @@ def targets(cost, base_cost) -> np.ndarray:
     return d.astype(np.float32)
 
 
-def collect(instances, iters: int, sample: int, seed: int = 100, n_cand: int | None = None, eps: float = 0.5):
-    """(X [N x 64] bf16 CUDA tensor, T [N] float32 CUDA tensor) from plain searches on `instances`."""
+def collect(instances, iters: int, sample: int, seed: int = 100, n_cand: int | None = None, eps: float = 0.5,
+            stride: int = 1):
+    """(X [N x 64] bf16 CUDA tensor, T [N] float32 CUDA tensor) from plain searches on `instances`: the
+    features and exact targets of `sample` candidates at `iters` points of each search, `stride`
+    iterations apart (a stride above 1 reaches the later, slower phase of the search)."""
     import torch
 
     xs, ts = [], []
@@ -48,7 +51,7 @@ def collect(instances, iters: int, sample: int, seed: int = 100, n_cand: int | N
             torch.cuda.synchronize()
             xs.append(feat.clone())
             ts.append(torch.tensor(targets(cost, float(bc.item())), device="cuda"))
-            S.search_step(1)
+            S.search_step(stride)
         S.close()
     return torch.cat(xs), torch.cat(ts)
 

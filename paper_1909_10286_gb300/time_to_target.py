@@ -165,7 +165,7 @@ def study_wall(workload: str = "large", seeds=range(5), n: int = 1 << 20, n_batc
                max_iters: int = 400, ref_iters: int = 4000, ref_n: int = 1 << 16, pool: int = 1 << 18,
                keep: int = 2359, rand_frac: float = 0.001, train_seeds=range(100, 104), train_iters: int = 30,
                train_sample: int = 8192, train_steps: int = 1500, tol: float = 0.01, eps: float = 0.5,
-               seed_offset: int = 1000, k_values=(1, 2), forms=None) -> dict:
+               seed_offset: int = 1000, k_values=(1, 2), forms=None, train_stride: int = 1) -> dict:
     """Time to within `tol` of the best cost, measured as host wall time through the API (every
     iteration a bl_search_step call and one read of every instance's C*), from handles already set up; set-up and the
     ranker's training are reported beside it, not counted. C_ref per instance is the best C* of a
@@ -230,7 +230,8 @@ def study_wall(workload: str = "large", seeds=range(5), n: int = 1 << 20, n_batc
 
     if want("learned_batched"):
         t1 = time.time()
-        X, T = learned.collect(I.make_batch(workload, train_seeds), iters=train_iters, sample=train_sample)
+        X, T = learned.collect(I.make_batch(workload, train_seeds), iters=train_iters, sample=train_sample,
+                               stride=train_stride)
         net, losses = learned.train(X, T, hidden=256, steps=train_steps, batch=4096, lr=1e-3,
                                     max_batch=pool * len(insts))
         t_train = time.time() - t1
