@@ -542,6 +542,12 @@ def main():
                 sub = measure_plain(args, wl, ws, rank, local, args.cpu_budget / 2)
                 line[wl] = {k: sub[k] for k in ("value", "unit", "ms_per_step", "config", "gpu_launches", "clocks",
                                                 "e2e", "roofline", "cpu_baseline") if k in sub}
+            # the batched workload also as one persistent launch for the whole batch (one handle), beside
+            # the default of one launch per launch-shape group
+            one = measure_plain(argparse.Namespace(**{**vars(args), "no_shape_split": True, "no_cpu_baseline": True}),
+                                "batched", ws, rank, local, 0.0)
+            line["batched"]["one_launch"] = {k: one[k] for k in ("value", "ms_per_step", "config", "gpu_launches",
+                                                                 "e2e", "roofline") if k in one}
             # ranked proposals on the paper-scale instance (the MLP's tensor-core roofline)
             sub = measure_learned(args, "learned", ws, rank, local)
             line["learned"] = {k: sub[k] for k in ("value", "unit", "ms_per_step", "config", "proposals_per_s",
