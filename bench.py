@@ -422,6 +422,8 @@ def measure_learned(args, workload, ws, rank, local):
     peaks = _peaks()
     peak = float(peaks.get("bf16_tflops", 1900.0))
     achieved = flop / (ms_mlp / 1e3) / 1e12
+    hbm_bytes = pool * (64 * 2 + 4)
+    hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f32 scorer, bf16 ranker", "data": "synthetic",
@@ -438,7 +440,12 @@ def measure_learned(args, workload, ws, rank, local):
                          "unit": "TFLOP/s", "frac": achieved / peak, "traffic": _traffic(workload),
                          "ms_per_launch": ms_mlp,
                          "flop_per_launch": flop,
-                         "peak_basis": "bf16_tflops (burst) of MEASURED_PEAKS.json; kernel timed alone"}}
+                         "peak_basis": "bf16_tflops (burst) of MEASURED_PEAKS.json; kernel timed alone",
+                         # the same launch against HBM: the features are materialised, so it reads them once
+                         # (BF16, 64 per row) and writes one FP32 prediction per row
+                         "hbm": {"achieved": hbm_bytes / (ms_mlp / 1e3) / 1e9, "peak": hbm_peak, "unit": "GB/s",
+                                 "frac": hbm_bytes / (ms_mlp / 1e3) / 1e9 / hbm_peak, "bytes_per_launch": hbm_bytes,
+                                 "peak_basis": "hbm_gbs of MEASURED_PEAKS.json"}}}
     net.close()
     S.close()
     if spec["compare_iters"] and rank == 0:
