@@ -56,7 +56,6 @@ class ShapedBatch:
         for h, g in enumerate(self.groups):
             for k, i in enumerate(g):
                 self._where[i] = (h, k)
-        self._outs = None
 
     @property
     def stream(self):
@@ -95,14 +94,13 @@ class ShapedBatch:
 
     def get_states(self, out=None) -> list:
         """Every instance's state, one bl_get_states transfer per group, in the batch's order. With `out`
-        (a list an earlier call returned) the same dicts are filled again."""
-        if out is None or self._outs is None:
-            self._outs = [S.get_states() for S in self.handles]
+        (state dicts as get_state returns, e.g. from an earlier call) those dicts are filled and returned."""
+        if out is None:
+            parts = [S.get_states() for S in self.handles]
         else:
-            for S, o in zip(self.handles, self._outs):
-                S.get_states(o)
+            parts = [S.get_states([out[i] for i in g]) for S, g in zip(self.handles, self.groups)]
         res = [None] * len(self.instances)
-        for g, o in zip(self.groups, self._outs):
+        for g, o in zip(self.groups, parts):
             for k, i in enumerate(g):
                 res[i] = o[k]
         return res
